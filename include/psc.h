@@ -1,0 +1,199 @@
+/* psc.h -- C ABI of the GB300 PET scatter Monte Carlo library (libpsc.so).
+ *
+ * The library computes the scatter estimate of Noe et al., "Object
+ * independent scatter sensitivities for PET, applied to scatter estimation
+ * through fast Monte Carlo simulation" (arXiv 2509.05047), Sec. 2.2:
+ * annihilation photon pairs are emitted from an activity image and
+ * transported through a known attenuation image (Sec. 2.3, step 2 of the
+ * joint estimation loop in Sec. 2.3.3), detected on a cylinder that keeps
+ * every photon crossing it (Sec. 2.2.1), weighted by the product of the two
+ * photons' 5D detection probabilities (Sec. 2.2.1-2.2.2), binned into an
+ * LOR x TOF sinogram, optionally smoothed with a normalisation sinogram
+ * (Sec. 2.3.2) and multiplied by the scatter-sensitivity sinogram
+ * (Sec. 2.2.4).
+ *
+ * Conventions
+ *   - Units: mm, keV, g/cm^3, cm^2/g, degrees.
+ *   - Every call returns PSC_OK (0) or a negative PSC_E* code; the message of
+ *     the calling thread's last failure is psc_last_error().  No exception or
+ *     abort crosses the ABI.
+ *   - "host" pointers are read during the call and may be freed after it;
+ *     "device" pointers are caller-owned CUDA device memory on the context's
+ *     device (for example a torch tensor's data_ptr()).
+ *   - Calls that take a stream enqueue work on it asynchronously; a NULL
+ *     stream is the legacy default stream.
+ *   - Objects (scanner, materials, phantom, LUT, sinogram, accumulator) are
+ *     copied to device memory owned by the context until psc_unload or
+ *     psc_destroy; they are identified by positive int32 ids.
+ *   - Array layouts: voxels [nz][ny][nx]; LUT [apos][tpos][E][alpha][beta];
+ *     sinograms [plane][view][radial][tof] with plane = ring_a * n_rings +
+ *     ring_b; per-LOR inputs [plane][view][radial] apply to every TOF bin.
+ */
+#ifndef PSC_H
+#define PSC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PSC_OK = 0,
+  PSC_EINVAL = -1,    /* invalid argument */
+  PSC_ENOMEM = -2,    /* device memory or admission budget exhausted */
+  PSC_ENOTFOUND = -3, /* unknown object id or wrong object kind */
+  PSC_ETIMEOUT = -4,  /* a bounded wait expired */
+  PSC_EDEVICE = -5,   /* CUDA error */
+  PSC_EOVERFLOW = -6  /* fixed-point headroom or size limit exceeded */
+};
+
+/* history classes (psc_stats.class_counts and listmode output) */
+enum {
+  PSC_CLASS_ABSORBED = 0,      /* a photon was photo-absorbed */
+  PSC_CLASS_LOST_AXIAL = 1,    /* a photon missed the cylinder's axial extent */
+  PSC_CLASS_ENERGY_WINDOW = 2, /* a photon's energy left [e_lo, e_hi] */
+  PSC_CLASS_STEP_LIMIT = 3,    /* safety bound of 4096 tracking steps reached */
+  PSC_CLASS_SAME_CRYSTAL = 4,  /* both photons in one transaxial crystal */
+  PSC_CLASS_OUT_OF_RANGE = 5,  /* TOF or clipped radial bin outside the sinogram */
+  PSC_CLASS_TRUE = 6,          /* both detected, neither interacted */
+  PSC_CLASS_SCATTER = 7        /* both detected, >= 1 Compton or Rayleigh event */
+};
+
+enum { PSC_LUT_F32 = 0, PSC_LUT_F16 = 1, PSC_LUT_BF16 = 2 };
+enum { PSC_BIN_SCATTER = 1, PSC_BIN_TRUES = 2 };
+
+typedef struct psc_ctx psc_ctx;
+typedef void* psc_stream; /* a cudaStream_t */
+
+/* Cylindrical scanner at the depth of interaction (Sec. 2.1.1, 2.2.1). */
+typedef struct {
+  double radius;        /* cylinder radius (mm) */
+  double ring_pitch;    /* axial ring pitch (mm); axial extent n_rings * ring_pitch, centred */
+  int32_t n_crystals;   /* crystals per ring, even; crystal c spans azimuth [2 pi c/N, 2 pi (c+1)/N) */
+  int32_t n_rings;
+  int32_t module_t;     /* LUT transaxial position = crystal mod module_t */
+  int32_t module_a;     /* LUT axial position = ring mod module_a */
+  double e_lo, e_hi;    /* energy window (keV) */
+  int32_t n_tof;        /* TOF bins of (l_a - l_b)/2, bin t covers [(t - n_tof/2) w, (t + 1 - n_tof/2) w) */
+  int32_t n_rad;        /* radial bins kept: centred clip of the n_crystals - 1 bins (same parity) */
+  double tof_bin_mm;    /* w (mm) */
+  double tof_sigma_mm;  /* Gaussian TOF blur sigma of (l_a - l_b)/2 (mm), 0 = none */
+} psc_scanner_desc;
+
+/* Materials: mass attenuation tables on the grid E = 0, 1, ..., n_e-1 keV
+ * (n_e >= 512), host arrays [n_mat][n_e]; 1 <= n_mat <= 8. */
+typedef struct {
+  int32_t n_mat;
+  int32_t n_e;
+  const double* compton;   /* host */
+  const double* rayleigh;  /* host */
+  const double* photo;     /* host */
+  const double* kappa;     /* host [n_mat]: Rayleigh form factor (1 + b s)^-2, b = kappa (E/511)^2 */
+} psc_materials_desc;
+
+/* Voxel phantom: attenuation (material id + density) and activity. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double dx, dy, dz;           /* voxel size (mm) */
+  double ox, oy, oz;           /* min corner of voxel (0,0,0) (mm); grid must lie inside the cylinder */
+  const uint8_t* material;     /* host [nz][ny][nx], ids < n_mat of the materials object */
+  const float* density;        /* host [nz][ny][nx] g/cm^3, >= 0 */
+  const float* activity;       /* host [nz][ny][nx], >= 0, positive sum */
+} psc_phantom_desc;
+
+/* 5D single-photon detection-probability LUT (Sec. 2.2.2). */
+typedef struct {
+  int32_t n_e, n_a, n_b;       /* energy, transaxial angle, axial angle bins */
+  int32_t n_tpos, n_apos;      /* must equal the scanner's module_t, module_a */
+  double e_min, e_max;         /* keV; nodes at bin centres */
+  double a_min, a_max;         /* deg */
+  double b_min, b_max;         /* deg */
+  int32_t dtype;               /* device storage: PSC_LUT_F32 / F16 / BF16 (rounded to nearest) */
+  const float* data;           /* host [n_apos][n_tpos][n_e][n_a][n_b] in [0, 1] */
+} psc_lut_desc;
+
+/* One simulation call (Sec. 2.2.1): histories [first_history,
+ * first_history + n_histories) of the counter-based random stream keyed by
+ * seed.  The result is independent of launch shape and of how the history
+ * range is split across calls. */
+typedef struct {
+  uint64_t seed;
+  uint64_t first_history;
+  uint64_t n_histories;
+  int32_t scanner, phantom, lut;   /* lut = 0: no LUT (every coincidence weighs 1) */
+  int32_t acc;                     /* accumulator to add into */
+  int32_t bin_mask;                /* PSC_BIN_SCATTER | PSC_BIN_TRUES; 0 = scatter */
+  int32_t block, grid;             /* launch shape; 0 = automatic */
+  int8_t* cls_out;                 /* device [n_histories] history class, or NULL */
+  int64_t* key_out;                /* device [n_histories] sinogram bin (-1 unless true/scatter), or NULL */
+  int64_t* q_out;                  /* device [n_histories] fixed-point weight rint(w 2^32), or NULL */
+} psc_sim_args;
+
+typedef struct {
+  uint64_t class_counts[8];
+  uint64_t steps;                  /* Woodcock tracking steps (real + virtual) */
+  uint64_t compton, rayleigh, photo;
+  uint64_t binned;                 /* events added to the accumulator */
+  uint64_t weight_sum;             /* sum of their fixed-point weights */
+} psc_stats;
+
+/* Sinogram post-processing (Sec. 2.2.4, 2.3.2). */
+typedef struct {
+  int32_t acc;
+  int32_t sens;                    /* sensitivity sinogram id, 0 = none (1) */
+  int32_t norm;                    /* smoothing-normalisation sinogram id, 0 = none */
+  int32_t smooth;                  /* 0: no smoothing; 1: sigma applies */
+  double sigma[3];                 /* Gaussian sigma in bins: radial, view, axial (within segment) */
+  double scale;                    /* global factor (e.g. 1/histories, decay, Sec. 2.4.3) */
+  int32_t sens_first;              /* 0 (paper order): smooth, then x sens; 1: x sens, then smooth */
+} psc_finalize_args;
+
+/* Context on one CUDA device.  mem_budget_bytes bounds the device memory of
+ * resident objects (0 = no bound). */
+int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes);
+void psc_destroy(psc_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none). */
+const char* psc_last_error(void);
+
+/* Scanner geometry (Sec. 2.1.1, 2.2.1). */
+int psc_load_scanner(psc_ctx* ctx, const psc_scanner_desc* desc, int32_t* id);
+/* Material cross-section tables (the simulator's physics input; Sec. 2.2.1). */
+int psc_load_materials(psc_ctx* ctx, const psc_materials_desc* desc, int32_t* id);
+/* Attenuation + activity images (Fig. "schematic sensitivities": the
+ * simulator's two inputs); builds the emission alias table (FP64) and the
+ * Woodcock majorant for this phantom. */
+int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* desc, int32_t materials, int32_t* id);
+/* New activity image for a loaded phantom (joint activity/scatter
+ * estimation, Sec. 2.3.3 step 2): rebuilds the alias table only. */
+int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity /* host */);
+/* Detection-probability LUT (Sec. 2.2.2); data == NULL loads a LUT of ones. */
+int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* desc, int32_t* id);
+/* Sensitivity (Sec. 2.2.4) or smoothing-normalisation (Sec. 2.3.2) sinogram
+ * for a scanner: host f64, per_lor = 1 for [plane][view][rad], 0 for the
+ * full [plane][view][rad][tof]. */
+int psc_load_sinogram(psc_ctx* ctx, int32_t scanner, const double* host, int32_t per_lor,
+                      int32_t* id);
+/* int64 fixed-point accumulator sinogram (weight w adds rint(w * 2^32)). */
+int psc_acc_create(psc_ctx* ctx, int32_t scanner, int32_t* id);
+int psc_acc_zero(psc_ctx* ctx, int32_t acc, psc_stream stream);
+/* Copy the raw accumulator out / in (checkpoint and resume): device int64
+ * arrays of the scanner's sinogram size. */
+int psc_acc_read(psc_ctx* ctx, int32_t acc, int64_t* out /* device */, psc_stream stream);
+int psc_acc_write(psc_ctx* ctx, int32_t acc, const int64_t* in /* device */, psc_stream stream);
+/* Simulate and accumulate (Sec. 2.2.1-2.2.3).  stats may be NULL; when
+ * given, the call waits for the stream and fills it. */
+int psc_simulate(psc_ctx* ctx, const psc_sim_args* args, psc_stats* stats, psc_stream stream);
+/* Scatter estimate = acc * scale * 2^-32, [x norm -> smooth -> / norm],
+ * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size). */
+int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
+                 psc_stream stream);
+/* Free one object. */
+int psc_unload(psc_ctx* ctx, int32_t id);
+/* Bytes of device memory held by the context's objects. */
+uint64_t psc_resident_bytes(const psc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

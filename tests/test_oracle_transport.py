@@ -52,18 +52,21 @@ def _unscattered_escape(rec, k):
         (rec["status"][:, k] != oracle.ABSORBED) & (rec["status"][:, k] != oracle.STEP_LIMIT)
 
 
-def test_uniform_box_survival_matches_independent_integral():
-    """Point-like source at the centre of a uniform box (density 1.3): the
+@pytest.mark.parametrize("material,density", [(W.MAT_WATER, 1.3), (W.MAT_BONE, 1.9)])
+def test_uniform_box_survival_matches_independent_integral(material, density):
+    """Point-like source at the centre of a uniform box: the
     fraction of photons leaving unscattered equals E[exp(-mu l)] over
     isotropic directions, l the exact ray-box distance; the fraction of
     true coincidences equals E[exp(-mu (l+ + l-)) 1{both hit}]."""
     mats = W.standard_materials()
-    ph = W.phantom_uniform_box(dims=(32, 32, 16), voxel=(4.0, 4.0, 4.0), density=1.3)
+    ph = W.phantom_uniform_box(dims=(32, 32, 16), voxel=(4.0, 4.0, 4.0), material=material,
+                               density=density)
     sc = W.scanner_tiny()
     n = 100_000
     r = oracle.simulate(sc, mats, ph, None, 21, 0, n, threads=8, records=True, bin_mask=3)
     rec = r["rec"]
-    mu = 1.3 * (mats[1].compton[511] + mats[1].rayleigh[511] + mats[1].photo[511]) / 10.0
+    mt = mats[material]
+    mu = density * (mt.compton[511] + mt.rayleigh[511] + mt.photo[511]) / 10.0
     rng = np.random.default_rng(123)
     m = 2_000_000
     p = rng.uniform(-4.0, 4.0, size=(m, 3))
@@ -91,12 +94,28 @@ def test_uniform_box_survival_matches_independent_integral():
     assert abs(got_true - expect_true) < 4 * sd
 
 
-def test_heterogeneous_survival_matches_exact_ray_sums():
-    """Torso with lungs (0.3 g/cc) and bone (1.9 g/cc): per photon, the
-    unscattered-escape indicator has the same mean as exp(-optical depth)
-    along its initial ray (paired comparison)."""
+def _slabs():
+    """Water / bone / lung slabs along x with activity everywhere."""
+    ph = W.phantom_uniform_box(dims=(48, 40, 24), voxel=(5.0, 5.0, 5.0), source="uniform")
+    ph.material[:, :, :16] = W.MAT_WATER
+    ph.density[:, :, :16] = 1.0
+    ph.material[:, :, 16:32] = W.MAT_BONE
+    ph.density[:, :, 16:32] = 1.9
+    ph.material[:, :, 32:] = W.MAT_LUNG
+    ph.density[:, :, 32:] = 0.3
+    return ph
+
+
+@pytest.mark.parametrize("which", ["torso", "slabs"])
+def test_heterogeneous_survival_matches_exact_ray_sums(which):
+    """Torso with lungs (0.3 g/cc) and bone (1.9 g/cc), and water/bone/lung
+    slabs: per photon, the unscattered-escape indicator has the same mean as
+    exp(-optical depth) along its initial ray (paired comparison)."""
     mats = W.standard_materials()
-    ph = W.phantom_torso(dims=(64, 64, 32), voxel=(4.68, 4.68, 5.56))
+    if which == "torso":
+        ph = W.phantom_torso(dims=(64, 64, 32), voxel=(4.68, 4.68, 5.56))
+    else:
+        ph = _slabs()
     sc = W.scanner_signa()
     n = 50_000
     rec = oracle.simulate(sc, mats, ph, None, 77, 0, n, threads=8, records=True)["rec"]
@@ -107,7 +126,7 @@ def test_heterogeneous_survival_matches_exact_ray_sums():
     tau = _optical_depth(p, d, mu, ph)
     diff = ind - np.exp(-tau)
     assert abs(diff.mean()) < 4 * diff.std() / math.sqrt(diff.size)
-    assert 0.2 < ind.mean() < 0.9
+    assert 0.1 < ind.mean() < 0.9
 
 
 def test_vacuum_photons_fly_straight_to_analytic_hits():
@@ -189,6 +208,25 @@ def test_invariants_tiny_configuration():
     expect = np.zeros(sc.n_bins, np.int64)
     np.add.at(expect, r["key"][sc_mask], r["q"][sc_mask])
     np.testing.assert_array_equal(r["acc"].ravel(), expect)
+
+
+def test_same_crystal_and_out_of_range_classes():
+    """Both photons detected: same transaxial crystal -> SAME_CRYSTAL, else a
+    bin or OUT_OF_RANGE (coarse 16-crystal ring, 3 TOF bins, dense water)."""
+    sc = W.scanner_small(n_crystals=16, n_rings=4, n_tof=3, tof_bin_mm=20.0, radius=120.0,
+                         e_lo=150.0)
+    ph = W.phantom_uniform_box(dims=(20, 20, 8), voxel=(4.0, 4.0, 4.0), density=2.0,
+                               source="uniform")
+    r = oracle.simulate(sc, W.standard_materials(), ph, None, 3, 0, 100_000, threads=8,
+                        records=True)
+    rec, cls = r["rec"], r["cls"]
+    both = (rec["status"] == oracle.DETECTED).all(1)
+    same = both & (rec["crystal"][:, 0] == rec["crystal"][:, 1])
+    det = (cls == oracle.TRUE) | (cls == oracle.SCATTER)
+    assert same.sum() > 10 and (cls == oracle.OUT_OF_RANGE).sum() > 50
+    np.testing.assert_array_equal(cls == oracle.SAME_CRYSTAL, same)
+    np.testing.assert_array_equal(both & ~same, det | (cls == oracle.OUT_OF_RANGE))
+    assert np.all(np.abs(rec["delta"][cls == oracle.OUT_OF_RANGE]) >= 30.0)
 
 
 def test_unit_lut_reduces_to_counts():
