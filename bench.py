@@ -1,0 +1,310 @@
+"""Benchmark: one step = zero accumulator -> simulate the paper-scale
+workload's histories -> finalize (3D Gaussian smoothing sigma = 2 bins,
+per-LOR sensitivity multiply) through the C ABI.
+
+Workload (paper scale): 128x128x89 torso phantom (2.34x2.34x2.78 mm, lungs,
+spine, 6 hot spheres 4:1), 448-crystal x 45-ring scanner (R 311.8 mm, 250.4
+mm), 27 TOF bins with 400 ps FWHM blur, FP32 LUT 64x32x32x16x9, 1e9
+histories per step.  Metric: photon-pair histories per second (whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--histories H]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "photon histories/s"
+UNIT = "histories/s"
+WORKLOAD = "paper-scale torso 128x128x89, scanner 448x45, 27 TOF (400 ps), LUT 64x32x32x16x9 f32, 1e9 histories/step, smoothing sigma=2, per-LOR sensitivity"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--histories", type=float, default=1e9)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.samples = []
+        self.stop = threading.Event()
+        self.t = None
+
+    def _run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.check_output(
+                    ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                     "--format=csv,noheader,nounits"], text=True, timeout=5)
+                self.samples.append([x.strip() for x in out.strip().split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > i + 2 and s[i + 2].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the transport kernel (lane operations), per counter;
+# derivation in DESIGN.md ("transport roofline")
+# ---------------------------------------------------------------------------
+OPS_PER_PHILOX_BLOCK = 100
+OPS_PER_STEP = 40
+OPS_PER_TRY = 15
+OPS_PER_INTERACTION = 45
+OPS_PER_DETECTION = 110
+OPS_PER_HISTORY = 60
+
+
+def transport_ops(st):
+    det = st["detected"]
+    hist = sum(st[c] for c in ("absorbed", "lost_axial", "energy_window", "step_limit",
+                                "same_crystal", "out_of_range", "true", "scatter"))
+    return (OPS_PER_PHILOX_BLOCK * st["rng_blocks"] + OPS_PER_STEP * st["steps"]
+            + OPS_PER_TRY * st["tries"] + OPS_PER_INTERACTION * (st["compton"] + st["rayleigh"])
+            + OPS_PER_DETECTION * det + OPS_PER_HISTORY * hist)
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def build_inputs():
+    sc = W.scanner_signa()
+    mats = W.standard_materials()
+    ph = W.phantom_torso()
+    lut = W.lut_signa(sc)
+    sens = W.sensitivity_uniform(sc.lor_shape, seed=1)
+    return sc, mats, ph, lut, sens
+
+
+def run_native(a):
+    import torch
+    import torch.distributed as dist
+    import paper_2509_05047_gb300 as psc
+    from paper_2509_05047_gb300 import build as B
+    B.build()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    sc, mats, ph, lut, sens = build_inputs()
+    n = int(a.histories)
+    ctx = psc.psc_create(local)
+    s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
+    m_id = psc.psc_load_materials(ctx, psc.materials_desc(mats).desc)
+    p_id = psc.psc_load_phantom(ctx, psc.phantom_desc(ph).desc, m_id)
+    l_id = psc.psc_load_lut(ctx, psc.lut_desc(lut).desc)
+    sn_id = psc.psc_load_sinogram(ctx, s_id, sens, per_lor=True)
+    a_id = psc.psc_acc_create(ctx, s_id)
+    out = torch.empty(sc.shape, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    seed = 20250905 + 7919 * rank           # each rank: its own independent request
+    fin = psc.finalize_args(a_id, sens=sn_id, sigma=(2.0, 2.0, 2.0), scale=1.0 / n)
+
+    def step(i, ev=None):
+        psc.psc_acc_zero(ctx, a_id, sh)
+        if ev is not None:
+            ev[0].record(stream)
+        psc.psc_simulate(ctx, psc.sim_args(seed, i * n, n, s_id, p_id, a_id, lut=l_id), stream=sh)
+        if ev is not None:
+            ev[1].record(stream)
+        psc.psc_finalize(ctx, fin, out, sh)
+
+    # counters of one step's transport (for the algorithmic-work roofline)
+    psc.psc_acc_zero(ctx, a_id, sh)
+    st = psc.psc_simulate(ctx, psc.sim_args(seed, 0, n, s_id, p_id, a_id, lut=l_id), stats=True,
+                          stream=sh)
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(a.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for i in range(a.steps):
+            step(a.warmup + i, evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    kern_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / a.steps
+    value = world * n * a.steps / (ms / 1e3)
+
+    # end to end through the host-buffer API: new activity image in (host),
+    # scatter estimate out to pinned host memory, every step
+    e2e = None
+    if not a.no_e2e and rank == 0:
+        host_out = torch.empty(sc.shape, dtype=torch.float64, pin_memory=True)
+        act = np.ascontiguousarray(ph.activity, dtype=np.float32)
+        torch.cuda.synchronize()
+        k = max(1, min(a.steps, 2))
+        t_start = time.perf_counter()
+        for i in range(k):
+            psc.psc_update_activity(ctx, p_id, act)
+            step(100 + i)
+            host_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = time.perf_counter() - t_start
+        e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": int(act.nbytes),
+               "d2h_bytes_per_step": int(out.numel() * 8)}
+        del host_out
+
+    peaks, src = measured_peaks()
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1485.0)
+    peak_ops = 152 * 128 * sm_mhz * 1e6                 # FP32/INT32 lane-ops per second
+    ops = transport_ops(st)
+    achieved = ops / (kern_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": round(achieved / 1e9, 1), "peak": round(peak_ops / 1e9, 1),
+                "unit": "Gop/s", "frac": round(achieved / peak_ops, 4), "traffic": None,
+                "kernel": "psc::transport_kernel<0>", "kernel_ms": round(kern_ms, 3),
+                "peak_source": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "histories_per_step": n, "global_batch": world * n,
+                      "l2": "inputs larger than L2 (43.8 GB accumulator + 43.8 GB output streamed every step)",
+                      "parallelism": f"replicas{world}"},
+           "roofline": roofline, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": 4 * a.steps,
+           "transport_stats": {k: int(v) for k, v in st.items()}}
+    if rank == 0 and not a.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(sc, mats, ph, lut, sens, n, budget_s=20.0)
+    psc.psc_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores (bounded sample, extrapolated to one step)
+# ---------------------------------------------------------------------------
+def cpu_baseline(sc, mats, ph, lut, sens, n, budget_s=20.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    alias = oracle.alias_build(ph.activity)
+    m = 20_000
+    t = time.perf_counter()
+    oracle.simulate(sc, mats, ph, lut, 1, 0, m, threads=cores, alias=alias)
+    per_h = (time.perf_counter() - t) / m
+    m = int(max(20_000, min(2_000_000, 0.6 * budget_s / max(per_h, 1e-9))))
+    t = time.perf_counter()
+    oracle.simulate(sc, mats, ph, lut, 2, 0, m, threads=cores, alias=alias)
+    per_h = (time.perf_counter() - t) / m
+    # finalize sample: the 25 planes of a 5-ring sub-scanner with the full
+    # view x radial x TOF extent
+    sub = np.random.default_rng(0).integers(0, 1 << 36, size=(25, sc.n_views, sc.n_rad, sc.n_tof))
+    t = time.perf_counter()
+    oracle.finalize(sub, 5, sens=sens[:25], sigma=(2.0, 2.0, 2.0), scale=1.0 / n)
+    per_bin = (time.perf_counter() - t) / sub.size
+    step_s = per_h * n + per_bin * sc.n_bins
+    return {"value": n / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{m} histories of the workload on {cores} threads ({per_h * 1e6:.3f} us each) + "
+                      f"finalize of {sub.size} bins ({per_bin * 1e9:.1f} ns each), extrapolated to "
+                      f"{n} histories and {sc.n_bins} bins per step"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    sc, mats, ph, lut, sens = build_inputs()
+    n = int(a.histories)
+    for _ in range(a.warmup):
+        pass
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        vals.append(cpu_baseline(sc, mats, ph, lut, sens, n, budget_s=8.0)["value"])
+    wall = time.perf_counter() - t0
+    v = float(np.median(vals))
+    cb = cpu_baseline.__doc__
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * n / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "histories_per_step": n},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: bounded oracle sample (~8 s) extrapolated to one step; wall {wall:.1f} s"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    res = run_reference(a) if a.impl == "reference" else run_native(a)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,9 @@ typedef struct {
   uint64_t compton, rayleigh, photo;
   uint64_t binned;                 /* events added to the accumulator */
   uint64_t weight_sum;             /* sum of their fixed-point weights */
+  uint64_t rng_blocks;             /* Philox4x32-10 blocks generated */
+  uint64_t tries;                  /* Compton and Rayleigh rejection-sampling tries */
+  uint64_t detected;               /* photons that reached the detector inside the window */
 } psc_stats;
 
 /* Sinogram post-processing (Sec. 2.2.4, 2.3.2). */

@@ -272,7 +272,7 @@ int orc_detect(const orc_scanner* sc, const double p[3], const double d[3], doub
   hit[2] = p[2] + t * d[2];
   *dist = t;
   double half = 0.5 * sc->n_rings * sc->ring_pitch;
-  if (hit[2] < -half || hit[2] >= half) return ORC_LOST_AXIAL;
+  if (!(hit[2] >= -half && hit[2] < half)) return ORC_LOST_AXIAL;
   int rg = (int)floor((hit[2] + half) / sc->ring_pitch);
   if (rg > sc->n_rings - 1) rg = sc->n_rings - 1;
   double phi = atan2(hit[1], hit[0]);

@@ -1,0 +1,298 @@
+"""Python binding of libpsc, the GB300 PET scatter Monte Carlo library.
+
+Thin ctypes marshalling over the C ABI in ``include/psc.h``: every function
+here has the name of the C entry point it calls and does no computation of
+its own.  Device buffers are passed as integer device pointers (for example
+``tensor.data_ptr()`` of a CUDA torch tensor) and streams as integer
+``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).
+Failures raise :class:`PscError` carrying the library's error code and
+message.  The library must have been built (``build.build()``); importing the
+binding without it fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsc.so")
+
+PSC_OK, PSC_EINVAL, PSC_ENOMEM, PSC_ENOTFOUND, PSC_ETIMEOUT, PSC_EDEVICE, PSC_EOVERFLOW = (
+    0, -1, -2, -3, -4, -5, -6)
+PSC_LUT_F32, PSC_LUT_F16, PSC_LUT_BF16 = 0, 1, 2
+PSC_BIN_SCATTER, PSC_BIN_TRUES = 1, 2
+CLASSES = ["absorbed", "lost_axial", "energy_window", "step_limit", "same_crystal",
+           "out_of_range", "true", "scatter"]
+
+
+class PscError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"psc error {code}: {msg}")
+        self.code = code
+
+
+class ScannerDesc(C.Structure):
+    _fields_ = [("radius", C.c_double), ("ring_pitch", C.c_double), ("n_crystals", C.c_int32),
+                ("n_rings", C.c_int32), ("module_t", C.c_int32), ("module_a", C.c_int32),
+                ("e_lo", C.c_double), ("e_hi", C.c_double), ("n_tof", C.c_int32),
+                ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double)]
+
+
+class MaterialsDesc(C.Structure):
+    _fields_ = [("n_mat", C.c_int32), ("n_e", C.c_int32), ("compton", C.c_void_p),
+                ("rayleigh", C.c_void_p), ("photo", C.c_void_p), ("kappa", C.c_void_p)]
+
+
+class PhantomDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double),
+                ("material", C.c_void_p), ("density", C.c_void_p), ("activity", C.c_void_p)]
+
+
+class LutDesc(C.Structure):
+    _fields_ = [("n_e", C.c_int32), ("n_a", C.c_int32), ("n_b", C.c_int32),
+                ("n_tpos", C.c_int32), ("n_apos", C.c_int32), ("e_min", C.c_double),
+                ("e_max", C.c_double), ("a_min", C.c_double), ("a_max", C.c_double),
+                ("b_min", C.c_double), ("b_max", C.c_double), ("dtype", C.c_int32),
+                ("data", C.c_void_p)]
+
+
+class SimArgs(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("first_history", C.c_uint64), ("n_histories", C.c_uint64),
+                ("scanner", C.c_int32), ("phantom", C.c_int32), ("lut", C.c_int32),
+                ("acc", C.c_int32), ("bin_mask", C.c_int32), ("block", C.c_int32),
+                ("grid", C.c_int32), ("cls_out", C.c_void_p), ("key_out", C.c_void_p),
+                ("q_out", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("class_counts", C.c_uint64 * 8), ("steps", C.c_uint64), ("compton", C.c_uint64),
+                ("rayleigh", C.c_uint64), ("photo", C.c_uint64), ("binned", C.c_uint64),
+                ("weight_sum", C.c_uint64), ("rng_blocks", C.c_uint64), ("tries", C.c_uint64),
+                ("detected", C.c_uint64)]
+
+    def as_dict(self):
+        d = {k: int(v) for k, v in zip(CLASSES, self.class_counts)}
+        for f in ("steps", "compton", "rayleigh", "photo", "binned", "weight_sum", "rng_blocks",
+                  "tries", "detected"):
+            d[f] = int(getattr(self, f))
+        return d
+
+
+class FinalizeArgs(C.Structure):
+    _fields_ = [("acc", C.c_int32), ("sens", C.c_int32), ("norm", C.c_int32),
+                ("smooth", C.c_int32), ("sigma", C.c_double * 3), ("scale", C.c_double),
+                ("sens_first", C.c_int32)]
+
+
+# exported entry points: name -> (restype, argtypes)
+_P, _I32, _U64 = C.c_void_p, C.c_int32, C.c_uint64
+SIGNATURES = {
+    "psc_create": (C.c_int, [C.POINTER(C.c_void_p), _I32, _U64]),
+    "psc_destroy": (None, [_P]),
+    "psc_last_error": (C.c_char_p, []),
+    "psc_load_scanner": (C.c_int, [_P, C.POINTER(ScannerDesc), C.POINTER(_I32)]),
+    "psc_load_materials": (C.c_int, [_P, C.POINTER(MaterialsDesc), C.POINTER(_I32)]),
+    "psc_load_phantom": (C.c_int, [_P, C.POINTER(PhantomDesc), _I32, C.POINTER(_I32)]),
+    "psc_update_activity": (C.c_int, [_P, _I32, _P]),
+    "psc_load_lut": (C.c_int, [_P, C.POINTER(LutDesc), C.POINTER(_I32)]),
+    "psc_load_sinogram": (C.c_int, [_P, _I32, _P, _I32, C.POINTER(_I32)]),
+    "psc_acc_create": (C.c_int, [_P, _I32, C.POINTER(_I32)]),
+    "psc_acc_zero": (C.c_int, [_P, _I32, _P]),
+    "psc_acc_read": (C.c_int, [_P, _I32, _P, _P]),
+    "psc_acc_write": (C.c_int, [_P, _I32, _P, _P]),
+    "psc_simulate": (C.c_int, [_P, C.POINTER(SimArgs), C.POINTER(Stats), _P]),
+    "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
+    "psc_unload": (C.c_int, [_P, _I32]),
+    "psc_resident_bytes": (_U64, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libpsc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(paper_2509_05047_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PSC_OK:
+        raise PscError(rc, psc_last_error())
+    return rc
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())  # torch tensor
+
+
+def _stream(s):
+    return None if s is None else int(s)
+
+
+# ---------------------------------------------------------------------------
+# C entry points
+# ---------------------------------------------------------------------------
+def psc_last_error():
+    return lib().psc_last_error().decode()
+
+
+def psc_create(device=0, mem_budget_bytes=0):
+    h = C.c_void_p()
+    _check(lib().psc_create(C.byref(h), device, mem_budget_bytes))
+    return h.value
+
+
+def psc_destroy(ctx):
+    lib().psc_destroy(ctx)
+
+
+def psc_resident_bytes(ctx):
+    return int(lib().psc_resident_bytes(ctx))
+
+
+def psc_load_scanner(ctx, desc: ScannerDesc):
+    i = C.c_int32()
+    _check(lib().psc_load_scanner(ctx, C.byref(desc), C.byref(i)))
+    return i.value
+
+
+def psc_load_materials(ctx, desc: MaterialsDesc):
+    i = C.c_int32()
+    _check(lib().psc_load_materials(ctx, C.byref(desc), C.byref(i)))
+    return i.value
+
+
+def psc_load_phantom(ctx, desc: PhantomDesc, materials):
+    i = C.c_int32()
+    _check(lib().psc_load_phantom(ctx, C.byref(desc), materials, C.byref(i)))
+    return i.value
+
+
+def psc_update_activity(ctx, phantom, activity):
+    a = np.ascontiguousarray(activity, dtype=np.float32)
+    _check(lib().psc_update_activity(ctx, phantom, a.ctypes.data))
+
+
+def psc_load_lut(ctx, desc: LutDesc):
+    i = C.c_int32()
+    _check(lib().psc_load_lut(ctx, C.byref(desc), C.byref(i)))
+    return i.value
+
+
+def psc_load_sinogram(ctx, scanner, host, per_lor):
+    h = np.ascontiguousarray(host, dtype=np.float64)
+    i = C.c_int32()
+    _check(lib().psc_load_sinogram(ctx, scanner, h.ctypes.data, 1 if per_lor else 0, C.byref(i)))
+    return i.value
+
+
+def psc_acc_create(ctx, scanner):
+    i = C.c_int32()
+    _check(lib().psc_acc_create(ctx, scanner, C.byref(i)))
+    return i.value
+
+
+def psc_acc_zero(ctx, acc, stream=None):
+    _check(lib().psc_acc_zero(ctx, acc, _stream(stream)))
+
+
+def psc_acc_read(ctx, acc, out, stream=None):
+    _check(lib().psc_acc_read(ctx, acc, _ptr(out), _stream(stream)))
+
+
+def psc_acc_write(ctx, acc, src, stream=None):
+    _check(lib().psc_acc_write(ctx, acc, _ptr(src), _stream(stream)))
+
+
+def psc_simulate(ctx, args: SimArgs, stats=False, stream=None):
+    st = Stats() if stats else None
+    _check(lib().psc_simulate(ctx, C.byref(args), C.byref(st) if st is not None else None,
+                              _stream(stream)))
+    return st.as_dict() if st is not None else None
+
+
+def psc_finalize(ctx, args: FinalizeArgs, out, stream=None):
+    _check(lib().psc_finalize(ctx, C.byref(args), _ptr(out), _stream(stream)))
+
+
+def psc_unload(ctx, obj):
+    _check(lib().psc_unload(ctx, obj))
+
+
+# ---------------------------------------------------------------------------
+# marshalling of the ``workloads`` input objects into descriptors
+# ---------------------------------------------------------------------------
+class _Held:
+    """A ctypes descriptor plus the host arrays it points into."""
+
+    def __init__(self, desc, *arrays):
+        self.desc = desc
+        self.arrays = arrays
+
+
+def scanner_desc(sc):
+    return ScannerDesc(sc.radius, sc.ring_pitch, sc.n_crystals, sc.n_rings, sc.module_t,
+                       sc.module_a, sc.e_lo, sc.e_hi, sc.n_tof, sc.n_rad, sc.tof_bin_mm,
+                       sc.tof_sigma_mm)
+
+
+def materials_desc(mats):
+    comp = np.ascontiguousarray(np.stack([m.compton for m in mats]), dtype=np.float64)
+    rayl = np.ascontiguousarray(np.stack([m.rayleigh for m in mats]), dtype=np.float64)
+    phot = np.ascontiguousarray(np.stack([m.photo for m in mats]), dtype=np.float64)
+    kap = np.ascontiguousarray([m.kappa for m in mats], dtype=np.float64)
+    d = MaterialsDesc(len(mats), comp.shape[1], comp.ctypes.data, rayl.ctypes.data,
+                      phot.ctypes.data, kap.ctypes.data)
+    return _Held(d, comp, rayl, phot, kap)
+
+
+def phantom_desc(ph):
+    mat = np.ascontiguousarray(ph.material, dtype=np.uint8)
+    den = np.ascontiguousarray(ph.density, dtype=np.float32)
+    act = np.ascontiguousarray(ph.activity, dtype=np.float32)
+    nx, ny, nz = ph.dims
+    d = PhantomDesc(nx, ny, nz, *ph.voxel, *ph.origin, mat.ctypes.data, den.ctypes.data,
+                    act.ctypes.data)
+    return _Held(d, mat, den, act)
+
+
+def lut_desc(lut, dtype=PSC_LUT_F32, ones=False):
+    data = None if ones else np.ascontiguousarray(lut.data, dtype=np.float32)
+    d = LutDesc(lut.n_e, lut.n_a, lut.n_b, lut.n_tpos, lut.n_apos, lut.e_min, lut.e_max,
+                lut.a_min, lut.a_max, lut.b_min, lut.b_max, dtype,
+                None if data is None else data.ctypes.data)
+    return _Held(d, data)
+
+
+def sim_args(seed, first, n, scanner, phantom, acc, lut=0, bin_mask=PSC_BIN_SCATTER, block=0,
+             grid=0, cls_out=None, key_out=None, q_out=None):
+    return SimArgs(seed, first, n, scanner, phantom, lut, acc, bin_mask, block, grid,
+                   _ptr(cls_out), _ptr(key_out), _ptr(q_out))
+
+
+def finalize_args(acc, sens=0, norm=0, sigma=None, scale=1.0, sens_first=False):
+    s = (C.c_double * 3)(*(sigma if sigma is not None else (0.0, 0.0, 0.0)))
+    return FinalizeArgs(acc, sens, norm, 1 if sigma is not None else 0, s, scale,
+                        1 if sens_first else 0)

@@ -1,0 +1,289 @@
+// psc_device.cuh -- device-side parameter blocks and the per-photon
+// arithmetic of the scatter Monte Carlo path (sm_103a).
+//
+// Shared by the transport and finalize translation units of libpsc only.
+// Everything here is FP32 transport arithmetic (FP64 only for the alias
+// probabilities and the sinogram post-processing), written for the GPU.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psc {
+
+constexpr int kMaxMaterials = 8;
+constexpr int kMaxSteps = 4096;     // Woodcock steps per photon (safety bound)
+constexpr int kMaxTries = 64;       // rejection-sampling tries, last proposal kept
+constexpr float kPolarEps = 1e-6f;  // |d_z| > 1 - eps: rotate about the z axis
+constexpr float kRestKeV = 511.0f;
+constexpr float kEmitKeV = 511.0f;
+constexpr int kMaxSmoothRadius = 64;
+
+enum : int {
+  kAbsorbed = 0, kLostAxial = 1, kEnergyWindow = 2, kStepLimit = 3,
+  kSameCrystal = 4, kOutOfRange = 5, kTrue = 6, kScatter = 7, kDetected = 15
+};
+
+// statistics slots (psc_stats order)
+enum : int {
+  kStatClass0 = 0, kStatSteps = 8, kStatCompton = 9, kStatRayleigh = 10, kStatPhoto = 11,
+  kStatBinned = 12, kStatWeight = 13, kStatRng = 14, kStatTries = 15, kStatDetected = 16,
+  kStatCount = 17
+};
+
+struct ScannerParams {
+  float radius, r2, half_len, inv_pitch;
+  float e_lo, e_hi;
+  float crystals_per_radian;   // N / (2 pi)
+  float inv_tof_bin, tof_half, tof_sigma;
+  int n_crystals, n_rings, module_t, module_a, n_tof, n_rad, n_views, rad_off;
+};
+
+struct PhantomParams {
+  int nx, ny, nz;
+  int n_mat, n_e;              // tables hold nodes E = 0 .. n_e - 1 keV
+  int n_tab, e0;               // nodes staged per launch: E = e0 .. e0 + n_tab - 1 keV
+  long long n_vox;
+  float ox, oy, oz, inv_dx, inv_dy, inv_dz, dx, dy, dz;
+  const float2* vox;           // {density, material id bits}
+  const double* alias_prob;
+  const int32_t* alias_idx;
+  const float4* xs;            // [n_mat][n_e] cumulative {C, C+R, C+R+P, 0} (mm^-1 per g/cm^3)
+  const float* maj;            // [n_e] Woodcock majorant (mm^-1), rounded up
+  const float* kappa;          // [n_mat]
+};
+
+struct LutParams {
+  const void* data;            // [n_apos][n_tpos][n_e][n_a][n_b], dtype below
+  int dtype;                   // -1 none, 0 f32, 1 f16, 2 bf16
+  int n_e, n_a, n_b, n_tpos, n_apos;
+  float e_min, e_scale, a_min, a_scale, b_min, b_scale;  // g = (x - min) * scale - 0.5
+};
+
+struct SimParams {
+  ScannerParams sc;
+  PhantomParams ph;
+  LutParams lut;
+  unsigned long long seed, first, n;
+  int bin_mask;
+  unsigned long long* acc;     // int64 fixed-point sinogram
+  int8_t* cls_out;
+  long long* key_out;
+  long long* q_out;
+  unsigned long long* stats;   // kStatCount counters or nullptr
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
+// multiplications, key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// uniform in (0,1): odd multiples of 2^-24 (exact in FP32)
+__device__ __forceinline__ float u01(uint32_t x) {
+  return (float)((x >> 9) * 2u + 1u) * 0x1p-24f;
+}
+
+// Sequential uniforms of one history's sub-stream: draw k is word k % 4 of
+// the Philox block with counter (history lo, history hi, k / 4, stream).
+struct Rng {
+  uint2 key;
+  uint32_t h0, h1, stream, block;
+  uint4 buf;
+  int left;
+
+  __device__ __forceinline__ void init(unsigned long long seed, unsigned long long hist, uint32_t s) {
+    key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    h0 = (uint32_t)hist;
+    h1 = (uint32_t)(hist >> 32);
+    stream = s;
+    block = 0;
+    left = 0;
+  }
+  __device__ __forceinline__ float next() {
+    if (left == 0) {
+      buf = philox4x32_10(make_uint4(h0, h1, block, stream), key);
+      ++block;
+      left = 4;
+    }
+    const uint32_t x = buf.x;
+    buf.x = buf.y;
+    buf.y = buf.z;
+    buf.z = buf.w;
+    --left;
+    return u01(x);
+  }
+};
+
+__device__ __forceinline__ uint4 philox_block(unsigned long long seed, unsigned long long hist,
+                                              uint32_t block, uint32_t stream) {
+  return philox4x32_10(make_uint4((uint32_t)hist, (uint32_t)(hist >> 32), block, stream),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// ---------------------------------------------------------------------------
+// Interaction sampling
+// ---------------------------------------------------------------------------
+
+// Klein-Nishina by Kahn's rejection method on x = E/E' in [1, 1 + 2a]:
+// branch A (probability (1+2a)/(9+2a)): x uniform, accept 4(x-1)/x^2;
+// branch B: x ~ 1/x^2, accept (cos^2 + 1/x)/2.
+__device__ __forceinline__ int sample_compton(Rng& r, float e, float& x, float& c) {
+  const float a = e / kRestKeV;
+  const float two_a = 2.0f * a;
+  const float p_a = (1.0f + two_a) / (9.0f + two_a);
+  x = 1.0f;
+  c = 1.0f;
+  int t = 0;
+  while (t < kMaxTries) {
+    ++t;
+    const float r1 = r.next(), r2 = r.next(), r3 = r.next();
+    bool accept;
+    if (r1 < p_a) {
+      x = 1.0f + two_a * r2;
+      c = 1.0f - (x - 1.0f) / a;
+      accept = r3 < 4.0f * (1.0f / x - 1.0f / (x * x));
+    } else {
+      x = (1.0f + two_a) / (1.0f + two_a * r2);
+      c = 1.0f - (x - 1.0f) / a;
+      accept = r3 < 0.5f * (c * c + 1.0f / x);
+    }
+    if (accept) break;
+  }
+  return t;
+}
+
+// Rayleigh: s = (1 - cos)/2 from (1 + b s)^-2 by inversion, accepted with
+// the Thomson factor (1 + cos^2)/2; b = kappa (E/511)^2.
+__device__ __forceinline__ float sample_rayleigh(Rng& r, float e, float kappa, int& tries) {
+  const float er = e / kRestKeV;
+  const float b = kappa * er * er;
+  float c = 1.0f;
+  int t = 0;
+  while (t < kMaxTries) {
+    ++t;
+    const float u1 = r.next(), u2 = r.next();
+    const float s = u1 / (1.0f + b * (1.0f - u1));
+    c = 1.0f - 2.0f * s;
+    if (u2 < 0.5f * (1.0f + c * c)) break;
+  }
+  tries = t;
+  return c;
+}
+
+// direction after scattering by polar cosine c and azimuth 2 pi u
+__device__ __forceinline__ void rotate(float3& d, float c, float u) {
+  const float sn = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+  float sp, cp;
+  sincospif(2.0f * u, &sp, &cp);
+  if (fabsf(d.z) > 1.0f - kPolarEps) {
+    const float sg = d.z > 0.0f ? 1.0f : -1.0f;
+    d = make_float3(sn * cp, sn * sp, sg * c);
+    return;
+  }
+  const float rr = sqrtf(1.0f - d.z * d.z);
+  const float nx = c * d.x + sn * (cp * d.x * d.z - sp * d.y) / rr;
+  const float ny = c * d.y + sn * (cp * d.y * d.z + sp * d.x) / rr;
+  const float nz = c * d.z - sn * cp * rr;
+  d = make_float3(nx, ny, nz);
+}
+
+// ---------------------------------------------------------------------------
+// Detection on the cylinder
+// ---------------------------------------------------------------------------
+struct Hit {
+  int status, crystal, ring;
+  float alpha, beta, dist;   // degrees, mm
+};
+
+__device__ __forceinline__ Hit detect(const ScannerParams& S, float3 p, float3 d, float e) {
+  Hit h;
+  h.crystal = 0;
+  h.ring = 0;
+  h.alpha = 0.0f;
+  h.beta = 0.0f;
+  h.dist = 0.0f;
+  const float a = d.x * d.x + d.y * d.y;
+  if (!(a > 0.0f)) { h.status = kLostAxial; return h; }
+  const float b = p.x * d.x + p.y * d.y;
+  const float c = p.x * p.x + p.y * p.y - S.r2;
+  const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
+  const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
+  const float hx = p.x + t * d.x, hy = p.y + t * d.y, hz = p.z + t * d.z;
+  h.dist = t;
+  if (!(hz >= -S.half_len && hz < S.half_len)) { h.status = kLostAxial; return h; }
+  h.ring = max(0, min((int)floorf((hz + S.half_len) * S.inv_pitch), S.n_rings - 1));
+  float phi = atan2f(hy, hx);
+  if (phi < 0.0f) phi += 6.283185307179586f;
+  h.crystal = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
+  const float nx = hx / S.radius, ny = hy / S.radius;
+  const float dn = d.x * nx + d.y * ny;
+  const float dt = -d.x * ny + d.y * nx;
+  h.alpha = atan2f(dt, dn) * 57.29577951308232f;
+  h.beta = atan2f(d.z, dn) * 57.29577951308232f;
+  h.status = (e < S.e_lo || e > S.e_hi) ? kEnergyWindow : kDetected;
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// 5D LUT: multilinear in (E, alpha, beta) on bin-centre nodes, clamped;
+// exact in the two crystal positions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lut_axis(float x, float lo, float scale, int n, int& i0, int& i1,
+                                         float& f) {
+  if (n == 1) { i0 = 0; i1 = 0; f = 0.0f; return; }
+  float g = (x - lo) * scale - 0.5f;
+  g = fminf(fmaxf(g, 0.0f), (float)(n - 1));
+  int i = min((int)g, n - 2);
+  i0 = i;
+  i1 = i + 1;
+  f = g - (float)i;
+}
+
+template <int DT>
+__device__ __forceinline__ float lut_load(const void* p, long long idx) {
+  if (DT == 0) return __ldg(reinterpret_cast<const float*>(p) + idx);
+  if (DT == 1) return __half2float(__ldg(reinterpret_cast<const __half*>(p) + idx));
+  return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p) + idx));
+}
+
+template <int DT>
+__device__ __forceinline__ float lut_prob(const LutParams& L, float e, float a, float b, int tpos,
+                                          int apos) {
+  if (DT < 0) return 1.0f;
+  int e0, e1, a0, a1, b0, b1;
+  float fe, fa, fb;
+  lut_axis(e, L.e_min, L.e_scale, L.n_e, e0, e1, fe);
+  lut_axis(a, L.a_min, L.a_scale, L.n_a, a0, a1, fa);
+  lut_axis(b, L.b_min, L.b_scale, L.n_b, b0, b1, fb);
+  const long long base = ((long long)apos * L.n_tpos + tpos) * L.n_e;
+  const long long r00 = ((base + e0) * L.n_a + a0) * L.n_b;
+  const long long r01 = ((base + e0) * L.n_a + a1) * L.n_b;
+  const long long r10 = ((base + e1) * L.n_a + a0) * L.n_b;
+  const long long r11 = ((base + e1) * L.n_a + a1) * L.n_b;
+  const float v000 = lut_load<DT>(L.data, r00 + b0), v001 = lut_load<DT>(L.data, r00 + b1);
+  const float v010 = lut_load<DT>(L.data, r01 + b0), v011 = lut_load<DT>(L.data, r01 + b1);
+  const float v100 = lut_load<DT>(L.data, r10 + b0), v101 = lut_load<DT>(L.data, r10 + b1);
+  const float v110 = lut_load<DT>(L.data, r11 + b0), v111 = lut_load<DT>(L.data, r11 + b1);
+  const float gb = 1.0f - fb, ga = 1.0f - fa, ge = 1.0f - fe;
+  const float w00 = gb * v000 + fb * v001, w01 = gb * v010 + fb * v011;
+  const float w10 = gb * v100 + fb * v101, w11 = gb * v110 + fb * v111;
+  const float w0 = ga * w00 + fa * w01, w1 = ga * w10 + fa * w11;
+  return ge * w0 + fe * w1;
+}
+
+}  // namespace psc

@@ -1,0 +1,39 @@
+// psc_internal.h -- declarations shared by the translation units of libpsc
+// (kernel launchers and their parameter blocks).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "psc_device.cuh"
+
+namespace psc {
+
+struct FinParams {
+  const long long* acc;
+  double* out;
+  float* scratch;              // FP32 sinogram-sized working buffer (smoothing only)
+  const double* sens;
+  const double* norm;
+  const double* rnorm;         // 1/norm, 0 where norm == 0
+  int sens_per_lor, norm_per_lor;
+  double c;                    // scale * 2^-32
+  long long n_bins;
+  int n_rings, V, R, T;
+  int smooth, sens_first;
+  int chunk_view, chunk_axial;
+  int K[3];                    // truncation radius per axis (radial, view, axial)
+  float g[3][2 * kMaxSmoothRadius + 1];
+};
+
+size_t transport_smem_bytes(const SimParams& p);
+cudaError_t launch_transport(const SimParams& p, int grid, int block, cudaStream_t s);
+cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm);
+
+size_t finalize_smem_radial(const FinParams& p);
+size_t finalize_smem_view(const FinParams& p);
+size_t finalize_smem_axial(const FinParams& p);
+cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s);
+cudaError_t launch_reciprocal(const double* a, double* r, long long n, int sms, cudaStream_t s);
+
+}  // namespace psc

@@ -1,0 +1,779 @@
+// runtime.cu -- host runtime and C ABI of libpsc (declared in include/psc.h).
+//
+// A context owns one device's resident state: scanners, material tables,
+// phantoms (packed voxels, FP64 alias table, per-phantom Woodcock majorant),
+// LUTs, sensitivity / normalisation sinograms and int64 accumulators.  Calls
+// validate their arguments, never throw across the ABI, and enqueue kernels
+// on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "psc.h"
+#include "psc_internal.h"
+
+using namespace psc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(PSC_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+  } while (0)
+
+enum Kind { kScannerObj = 1, kMaterialsObj, kPhantomObj, kLutObj, kSinoObj, kAccObj };
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+struct Object {
+  int kind;
+  size_t bytes = 0;
+  explicit Object(int k) : kind(k) {}
+  virtual ~Object() = default;
+};
+
+struct ScannerObj : Object {
+  psc_scanner_desc desc;
+  ScannerParams params;
+  long long n_bins = 0, n_lor = 0;
+  ScannerObj() : Object(kScannerObj) {}
+};
+
+struct MaterialsObj : Object {
+  int n_mat = 0, n_e = 0;
+  std::vector<double> comp, rayl, phot, kappa;
+  MaterialsObj() : Object(kMaterialsObj) {}
+};
+
+struct PhantomObj : Object {
+  psc_phantom_desc desc;  // host pointers cleared
+  int n_mat = 0, n_e = 0;
+  long long n_vox = 0;
+  DevBuf vox, alias_prob, alias_idx, xs, maj, kappa;
+  PhantomObj() : Object(kPhantomObj) {}
+};
+
+struct LutObj : Object {
+  psc_lut_desc desc;
+  DevBuf data;
+  LutParams params;
+  LutObj() : Object(kLutObj) {}
+};
+
+struct SinoObj : Object {
+  int32_t scanner = 0;
+  int per_lor = 0;
+  long long n = 0;
+  DevBuf data, recip;
+  SinoObj() : Object(kSinoObj) {}
+};
+
+struct AccObj : Object {
+  int32_t scanner = 0;
+  long long n = 0;
+  DevBuf data;
+  AccObj() : Object(kAccObj) {}
+};
+
+// device guard: make the context's device current for the call
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct psc_ctx {
+  int device = 0;
+  int sms = 0;
+  int max_smem_optin = 0;
+  uint64_t budget = 0;
+  uint64_t resident = 0;
+  std::mutex mu;
+  int32_t next_id = 1;
+  std::unordered_map<int32_t, std::shared_ptr<Object>> objs;
+  // finalize working buffer (FP32, sinogram-sized), grown on demand; its
+  // users are ordered on the GPU through scratch_done (the last smoothing
+  // pass that wrote it), so calls on different streams never overlap on it
+  std::mutex scratch_mu;
+  DevBuf scratch;
+  cudaEvent_t scratch_done = nullptr;
+  // statistics counters of psc_simulate (used only when stats are requested)
+  std::mutex stats_mu;
+  DevBuf stats;
+};
+
+namespace {
+
+int dev_alloc(psc_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->budget && ctx->resident + bytes > ctx->budget)
+      return fail(PSC_ENOMEM, "device memory budget exceeded (%llu + %llu > %llu bytes)",
+                  (unsigned long long)ctx->resident, (unsigned long long)bytes,
+                  (unsigned long long)ctx->budget);
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(PSC_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return PSC_OK;
+}
+
+int32_t add_object(psc_ctx* ctx, std::shared_ptr<Object> o) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  const int32_t id = ctx->next_id++;
+  ctx->resident += o->bytes;
+  ctx->objs.emplace(id, std::move(o));
+  return id;
+}
+
+template <class T>
+std::shared_ptr<T> get(psc_ctx* ctx, int32_t id, int kind) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->objs.find(id);
+  if (it == ctx->objs.end() || it->second->kind != kind) return nullptr;
+  return std::static_pointer_cast<T>(it->second);
+}
+
+const char* kind_name(int k) {
+  switch (k) {
+    case kScannerObj: return "scanner";
+    case kMaterialsObj: return "materials";
+    case kPhantomObj: return "phantom";
+    case kLutObj: return "lut";
+    case kSinoObj: return "sinogram";
+    case kAccObj: return "accumulator";
+  }
+  return "object";
+}
+
+#define GET(T, var, id, kind)                                                     \
+  auto var = get<T>(ctx, id, kind);                                               \
+  if (!var) return fail(PSC_ENOTFOUND, "no %s with id %d", kind_name(kind), (int)(id))
+
+// ---------------------------------------------------------------------------
+// Vose's alias method (Vose 1991) in FP64 with a fixed work-list order:
+// scaled weights n * a_i / sum, indices pushed in ascending order onto a
+// "small" (< 1) or "large" stack, pairs popped from the tops; leftovers get
+// probability 1.
+// ---------------------------------------------------------------------------
+int build_alias(const float* a, long long n, std::vector<double>& prob, std::vector<int32_t>& alias) {
+  double sum = 0.0;
+  for (long long i = 0; i < n; ++i) {
+    const double v = (double)a[i];
+    if (!(v >= 0.0) || !std::isfinite(v)) return fail(PSC_EINVAL, "activity[%lld] is negative or not finite", i);
+    sum += v;
+  }
+  if (!(sum > 0.0) || !std::isfinite(sum)) return fail(PSC_EINVAL, "activity has no positive finite sum");
+  prob.assign((size_t)n, 0.0);
+  alias.assign((size_t)n, 0);
+  std::vector<double> p((size_t)n);
+  std::vector<int32_t> small, large;
+  small.reserve((size_t)n);
+  large.reserve((size_t)n);
+  for (long long i = 0; i < n; ++i) {
+    p[i] = ((double)a[i] * (double)n) / sum;
+    (p[i] < 1.0 ? small : large).push_back((int32_t)i);
+  }
+  while (!small.empty() && !large.empty()) {
+    const int32_t s = small.back();
+    small.pop_back();
+    const int32_t l = large.back();
+    large.pop_back();
+    prob[s] = p[s];
+    alias[s] = l;
+    p[l] = (p[l] + p[s]) - 1.0;
+    (p[l] < 1.0 ? small : large).push_back(l);
+  }
+  while (!large.empty()) {
+    const int32_t l = large.back();
+    large.pop_back();
+    prob[l] = 1.0;
+    alias[l] = l;
+  }
+  while (!small.empty()) {
+    const int32_t s = small.back();
+    small.pop_back();
+    prob[s] = 1.0;
+    alias[s] = s;
+  }
+  return PSC_OK;
+}
+
+float round_up_f32(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+int check_scanner(const psc_scanner_desc* d) {
+  if (!d) return fail(PSC_EINVAL, "scanner desc is NULL");
+  if (d->n_crystals < 4 || (d->n_crystals & 1)) return fail(PSC_EINVAL, "n_crystals must be even and >= 4");
+  if (d->n_rings < 1 || d->n_tof < 1) return fail(PSC_EINVAL, "n_rings and n_tof must be >= 1");
+  if (d->n_rad < 1 || d->n_rad > d->n_crystals - 1 || ((d->n_crystals - 1 - d->n_rad) & 1))
+    return fail(PSC_EINVAL, "n_rad must be in [1, n_crystals-1] with n_crystals-1-n_rad even");
+  if (!(d->radius > 0) || !(d->ring_pitch > 0) || !(d->tof_bin_mm > 0) || !(d->tof_sigma_mm >= 0))
+    return fail(PSC_EINVAL, "radius, ring_pitch, tof_bin_mm must be > 0 and tof_sigma_mm >= 0");
+  if (d->module_t < 1 || d->module_a < 1) return fail(PSC_EINVAL, "module sizes must be >= 1");
+  if (!(d->e_hi >= d->e_lo) || !(d->e_lo >= 0)) return fail(PSC_EINVAL, "bad energy window");
+  return PSC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* psc_last_error(void) { return g_err.c_str(); }
+
+int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
+  if (!out) return fail(PSC_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(PSC_EINVAL, "device %d out of range (%d devices)", device, n);
+  psc_ctx* ctx = new (std::nothrow) psc_ctx();
+  if (!ctx) return fail(PSC_ENOMEM, "host allocation failed");
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  DeviceGuard g(device);
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaGetDeviceProperties");
+  }
+  ctx->sms = prop.multiProcessorCount;
+  ctx->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
+  e = cudaMalloc(&ctx->stats.p, sizeof(unsigned long long) * kStatCount);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaMalloc(stats)");
+  }
+  ctx->stats.bytes = sizeof(unsigned long long) * kStatCount;
+  e = cudaEventCreateWithFlags(&ctx->scratch_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  *out = ctx;
+  return PSC_OK;
+}
+
+void psc_destroy(psc_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
+  delete ctx;
+}
+
+uint64_t psc_resident_bytes(const psc_ctx* ctx) { return ctx ? ctx->resident : 0; }
+
+int psc_load_scanner(psc_ctx* ctx, const psc_scanner_desc* d, int32_t* id) {
+  if (!ctx || !id) return fail(PSC_EINVAL, "ctx or id is NULL");
+  int rc = check_scanner(d);
+  if (rc) return rc;
+  auto o = std::make_shared<ScannerObj>();
+  o->desc = *d;
+  ScannerParams& s = o->params;
+  s.radius = (float)d->radius;
+  s.r2 = (float)(d->radius * d->radius);
+  s.half_len = (float)(0.5 * d->n_rings * d->ring_pitch);
+  s.inv_pitch = (float)(1.0 / d->ring_pitch);
+  s.e_lo = (float)d->e_lo;
+  s.e_hi = (float)d->e_hi;
+  s.crystals_per_radian = (float)(d->n_crystals / (2.0 * M_PI));
+  s.inv_tof_bin = (float)(1.0 / d->tof_bin_mm);
+  s.tof_half = (float)(0.5 * d->n_tof);
+  s.tof_sigma = (float)d->tof_sigma_mm;
+  s.n_crystals = d->n_crystals;
+  s.n_rings = d->n_rings;
+  s.module_t = d->module_t;
+  s.module_a = d->module_a;
+  s.n_tof = d->n_tof;
+  s.n_rad = d->n_rad;
+  s.n_views = d->n_crystals / 2;
+  s.rad_off = (d->n_crystals - 1 - d->n_rad) / 2;
+  o->n_lor = (long long)d->n_rings * d->n_rings * s.n_views * d->n_rad;
+  o->n_bins = o->n_lor * d->n_tof;
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+int psc_load_materials(psc_ctx* ctx, const psc_materials_desc* d, int32_t* id) {
+  if (!ctx || !id || !d) return fail(PSC_EINVAL, "NULL argument");
+  if (d->n_mat < 1 || d->n_mat > kMaxMaterials) return fail(PSC_EINVAL, "n_mat must be in [1, %d]", kMaxMaterials);
+  if (d->n_e < 512) return fail(PSC_EINVAL, "n_e must be >= 512 (nodes 0..511 keV at least)");
+  if (!d->compton || !d->rayleigh || !d->photo || !d->kappa) return fail(PSC_EINVAL, "NULL table");
+  auto o = std::make_shared<MaterialsObj>();
+  const size_t n = (size_t)d->n_mat * d->n_e;
+  o->n_mat = d->n_mat;
+  o->n_e = d->n_e;
+  o->comp.assign(d->compton, d->compton + n);
+  o->rayl.assign(d->rayleigh, d->rayleigh + n);
+  o->phot.assign(d->photo, d->photo + n);
+  o->kappa.assign(d->kappa, d->kappa + d->n_mat);
+  for (size_t i = 0; i < n; ++i)
+    if (!(o->comp[i] >= 0) || !(o->rayl[i] >= 0) || !(o->phot[i] >= 0) || !std::isfinite(o->comp[i] + o->rayl[i] + o->phot[i]))
+      return fail(PSC_EINVAL, "cross-section table entry %zu negative or not finite", i);
+  for (int m = 0; m < d->n_mat; ++m)
+    if (!(o->kappa[m] >= 0) || !std::isfinite(o->kappa[m])) return fail(PSC_EINVAL, "kappa[%d] invalid", m);
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+static int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
+  std::vector<double> prob;
+  std::vector<int32_t> alias;
+  int rc = build_alias(activity, o->n_vox, prob, alias);
+  if (rc) return rc;
+  CK(cudaMemcpy(o->alias_prob.p, prob.data(), sizeof(double) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
+  CK(cudaMemcpy(o->alias_idx.p, alias.data(), sizeof(int32_t) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
+  (void)ctx;
+  return PSC_OK;
+}
+
+int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* d, int32_t materials, int32_t* id) {
+  if (!ctx || !id || !d) return fail(PSC_EINVAL, "NULL argument");
+  GET(MaterialsObj, mat, materials, kMaterialsObj);
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(PSC_EINVAL, "phantom dims must be >= 1");
+  const long long nv = (long long)d->nx * d->ny * d->nz;
+  if (nv > (1LL << 31) - 1) return fail(PSC_EOVERFLOW, "phantom has more than 2^31-1 voxels");
+  if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return fail(PSC_EINVAL, "voxel sizes must be > 0");
+  if (!d->material || !d->density || !d->activity) return fail(PSC_EINVAL, "NULL phantom array");
+  DeviceGuard g(ctx->device);
+  auto o = std::make_shared<PhantomObj>();
+  o->desc = *d;
+  o->desc.material = nullptr;
+  o->desc.density = nullptr;
+  o->desc.activity = nullptr;
+  o->n_vox = nv;
+  o->n_mat = mat->n_mat;
+  o->n_e = mat->n_e;
+  // packed voxels and the densest voxel per material
+  std::vector<float2> vox((size_t)nv);
+  std::vector<double> rho_max((size_t)mat->n_mat, 0.0);
+  for (long long v = 0; v < nv; ++v) {
+    const int m = d->material[v];
+    const float r = d->density[v];
+    if (m >= mat->n_mat) return fail(PSC_EINVAL, "material[%lld] = %d >= n_mat", v, m);
+    if (!(r >= 0.0f) || !std::isfinite(r)) return fail(PSC_EINVAL, "density[%lld] invalid", v);
+    int bits = m;
+    float fm;
+    std::memcpy(&fm, &bits, sizeof fm);
+    vox[v] = make_float2(r, fm);
+    if ((double)r > rho_max[m]) rho_max[m] = (double)r;
+  }
+  // cumulative cross sections (mm^-1 per g/cm^3) and the Woodcock majorant
+  const int ne = mat->n_e;
+  std::vector<float4> xs((size_t)mat->n_mat * ne);
+  std::vector<float> maj((size_t)ne);
+  for (int m = 0; m < mat->n_mat; ++m)
+    for (int k = 0; k < ne; ++k) {
+      const double c = mat->comp[(size_t)m * ne + k], r = mat->rayl[(size_t)m * ne + k],
+                   p = mat->phot[(size_t)m * ne + k];
+      xs[(size_t)m * ne + k] = make_float4((float)(c / 10.0), (float)((c + r) / 10.0), (float)((c + r + p) / 10.0), 0.0f);
+    }
+  for (int k = 0; k < ne; ++k) {
+    double best = 0.0;
+    for (int m = 0; m < mat->n_mat; ++m) {
+      const double tot = mat->comp[(size_t)m * ne + k] + mat->rayl[(size_t)m * ne + k] + mat->phot[(size_t)m * ne + k];
+      const double mu = rho_max[m] * tot / 10.0;
+      if (mu > best) best = mu;
+    }
+    maj[k] = round_up_f32(best);
+  }
+  std::vector<float> kap(kMaxMaterials, 0.0f);
+  for (int m = 0; m < mat->n_mat; ++m) kap[m] = (float)mat->kappa[m];
+  int rc;
+  if ((rc = dev_alloc(ctx, o->vox, sizeof(float2) * nv))) return rc;
+  if ((rc = dev_alloc(ctx, o->alias_prob, sizeof(double) * nv))) return rc;
+  if ((rc = dev_alloc(ctx, o->alias_idx, sizeof(int32_t) * nv))) return rc;
+  if ((rc = dev_alloc(ctx, o->xs, sizeof(float4) * xs.size()))) return rc;
+  if ((rc = dev_alloc(ctx, o->maj, sizeof(float) * ne))) return rc;
+  if ((rc = dev_alloc(ctx, o->kappa, sizeof(float) * kMaxMaterials))) return rc;
+  o->bytes = o->vox.bytes + o->alias_prob.bytes + o->alias_idx.bytes + o->xs.bytes + o->maj.bytes + o->kappa.bytes;
+  CK(cudaMemcpy(o->vox.p, vox.data(), sizeof(float2) * nv, cudaMemcpyHostToDevice), "upload voxels");
+  CK(cudaMemcpy(o->xs.p, xs.data(), sizeof(float4) * xs.size(), cudaMemcpyHostToDevice), "upload tables");
+  CK(cudaMemcpy(o->maj.p, maj.data(), sizeof(float) * ne, cudaMemcpyHostToDevice), "upload majorant");
+  CK(cudaMemcpy(o->kappa.p, kap.data(), sizeof(float) * kMaxMaterials, cudaMemcpyHostToDevice), "upload kappa");
+  if ((rc = upload_alias(ctx, o.get(), d->activity))) return rc;
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity) {
+  if (!ctx || !activity) return fail(PSC_EINVAL, "NULL argument");
+  GET(PhantomObj, ph, phantom, kPhantomObj);
+  DeviceGuard g(ctx->device);
+  CK(cudaDeviceSynchronize(), "synchronize before activity update");
+  return upload_alias(ctx, ph.get(), activity);
+}
+
+int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* d, int32_t* id) {
+  if (!ctx || !id || !d) return fail(PSC_EINVAL, "NULL argument");
+  if (d->n_e < 1 || d->n_a < 1 || d->n_b < 1 || d->n_tpos < 1 || d->n_apos < 1)
+    return fail(PSC_EINVAL, "LUT axis sizes must be >= 1");
+  if (!(d->e_max > d->e_min) || !(d->a_max > d->a_min) || !(d->b_max > d->b_min))
+    return fail(PSC_EINVAL, "LUT axis ranges must be increasing");
+  if (d->dtype < PSC_LUT_F32 || d->dtype > PSC_LUT_BF16) return fail(PSC_EINVAL, "unknown LUT dtype %d", d->dtype);
+  const long long n = (long long)d->n_e * d->n_a * d->n_b * d->n_tpos * d->n_apos;
+  DeviceGuard g(ctx->device);
+  auto o = std::make_shared<LutObj>();
+  o->desc = *d;
+  o->desc.data = nullptr;
+  const size_t esz = d->dtype == PSC_LUT_F32 ? 4 : 2;
+  std::vector<unsigned char> host((size_t)n * esz);
+  for (long long i = 0; i < n; ++i) {
+    const float v = d->data ? d->data[i] : 1.0f;
+    if (!(v >= 0.0f && v <= 1.0f)) return fail(PSC_EINVAL, "LUT value %lld = %g outside [0, 1]", i, (double)v);
+    if (d->dtype == PSC_LUT_F32) {
+      std::memcpy(&host[(size_t)i * 4], &v, 4);
+    } else if (d->dtype == PSC_LUT_F16) {
+      const __half h = __float2half_rn(v);
+      std::memcpy(&host[(size_t)i * 2], &h, 2);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      std::memcpy(&host[(size_t)i * 2], &h, 2);
+    }
+  }
+  int rc;
+  if ((rc = dev_alloc(ctx, o->data, host.size()))) return rc;
+  o->bytes = o->data.bytes;
+  CK(cudaMemcpy(o->data.p, host.data(), host.size(), cudaMemcpyHostToDevice), "upload LUT");
+  LutParams& L = o->params;
+  L.data = o->data.p;
+  L.dtype = d->dtype;
+  L.n_e = d->n_e;
+  L.n_a = d->n_a;
+  L.n_b = d->n_b;
+  L.n_tpos = d->n_tpos;
+  L.n_apos = d->n_apos;
+  L.e_min = (float)d->e_min;
+  L.e_scale = (float)(d->n_e / (d->e_max - d->e_min));
+  L.a_min = (float)d->a_min;
+  L.a_scale = (float)(d->n_a / (d->a_max - d->a_min));
+  L.b_min = (float)d->b_min;
+  L.b_scale = (float)(d->n_b / (d->b_max - d->b_min));
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+int psc_load_sinogram(psc_ctx* ctx, int32_t scanner, const double* host, int32_t per_lor, int32_t* id) {
+  if (!ctx || !id || !host) return fail(PSC_EINVAL, "NULL argument");
+  GET(ScannerObj, sc, scanner, kScannerObj);
+  DeviceGuard g(ctx->device);
+  auto o = std::make_shared<SinoObj>();
+  o->scanner = scanner;
+  o->per_lor = per_lor ? 1 : 0;
+  o->n = per_lor ? sc->n_lor : sc->n_bins;
+  int rc;
+  if ((rc = dev_alloc(ctx, o->data, sizeof(double) * o->n))) return rc;
+  o->bytes = o->data.bytes;
+  CK(cudaMemcpy(o->data.p, host, sizeof(double) * o->n, cudaMemcpyHostToDevice), "upload sinogram");
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+int psc_acc_create(psc_ctx* ctx, int32_t scanner, int32_t* id) {
+  if (!ctx || !id) return fail(PSC_EINVAL, "NULL argument");
+  GET(ScannerObj, sc, scanner, kScannerObj);
+  DeviceGuard g(ctx->device);
+  auto o = std::make_shared<AccObj>();
+  o->scanner = scanner;
+  o->n = sc->n_bins;
+  int rc;
+  if ((rc = dev_alloc(ctx, o->data, sizeof(long long) * o->n))) return rc;
+  o->bytes = o->data.bytes;
+  CK(cudaMemset(o->data.p, 0, sizeof(long long) * o->n), "zero accumulator");
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
+int psc_acc_zero(psc_ctx* ctx, int32_t acc, psc_stream stream) {
+  if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
+  GET(AccObj, a, acc, kAccObj);
+  DeviceGuard g(ctx->device);
+  CK(cudaMemsetAsync(a->data.p, 0, sizeof(long long) * a->n, (cudaStream_t)stream), "zero accumulator");
+  return PSC_OK;
+}
+
+int psc_acc_read(psc_ctx* ctx, int32_t acc, int64_t* out, psc_stream stream) {
+  if (!ctx || !out) return fail(PSC_EINVAL, "NULL argument");
+  GET(AccObj, a, acc, kAccObj);
+  DeviceGuard g(ctx->device);
+  CK(cudaMemcpyAsync(out, a->data.p, sizeof(long long) * a->n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "read accumulator");
+  return PSC_OK;
+}
+
+int psc_acc_write(psc_ctx* ctx, int32_t acc, const int64_t* in, psc_stream stream) {
+  if (!ctx || !in) return fail(PSC_EINVAL, "NULL argument");
+  GET(AccObj, a, acc, kAccObj);
+  DeviceGuard g(ctx->device);
+  CK(cudaMemcpyAsync(a->data.p, in, sizeof(long long) * a->n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "write accumulator");
+  return PSC_OK;
+}
+
+int psc_unload(psc_ctx* ctx, int32_t id) {
+  if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
+  std::shared_ptr<Object> o;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->objs.find(id);
+    if (it == ctx->objs.end()) return fail(PSC_ENOTFOUND, "no object with id %d", (int)id);
+    o = it->second;
+    ctx->objs.erase(it);
+    ctx->resident -= o->bytes;
+  }
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();  // no kernel may still read it
+  o.reset();
+  return PSC_OK;
+}
+
+int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stream stream) {
+  if (!ctx || !a) return fail(PSC_EINVAL, "NULL argument");
+  GET(ScannerObj, sc, a->scanner, kScannerObj);
+  GET(PhantomObj, ph, a->phantom, kPhantomObj);
+  GET(AccObj, acc, a->acc, kAccObj);
+  std::shared_ptr<LutObj> lut;
+  if (a->lut != 0) {
+    lut = get<LutObj>(ctx, a->lut, kLutObj);
+    if (!lut) return fail(PSC_ENOTFOUND, "no lut with id %d", (int)a->lut);
+    if (lut->desc.n_tpos != sc->desc.module_t || lut->desc.n_apos != sc->desc.module_a)
+      return fail(PSC_EINVAL, "LUT positions (%d, %d) do not match scanner modules (%d, %d)",
+                  lut->desc.n_tpos, lut->desc.n_apos, sc->desc.module_t, sc->desc.module_a);
+  }
+  if (acc->scanner != a->scanner) return fail(PSC_EINVAL, "accumulator belongs to scanner %d", (int)acc->scanner);
+  if (a->first_history + a->n_histories < a->first_history) return fail(PSC_EOVERFLOW, "history range wraps");
+  if (a->bin_mask < 0 || a->bin_mask > 3) return fail(PSC_EINVAL, "bin_mask must be in [0, 3]");
+  if (a->block < 0 || a->block > 1024 || (a->block % 32) || a->grid < 0)
+    return fail(PSC_EINVAL, "block must be a multiple of 32 in [32, 1024], grid >= 0");
+  const psc_phantom_desc& pd = ph->desc;
+  const double R2 = sc->desc.radius * sc->desc.radius;
+  for (int i = 0; i < 4; ++i) {
+    const double x = pd.ox + ((i & 1) ? pd.nx * pd.dx : 0.0), y = pd.oy + ((i & 2) ? pd.ny * pd.dy : 0.0);
+    if (!(x * x + y * y < R2)) return fail(PSC_EINVAL, "phantom grid reaches outside the detector cylinder");
+  }
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (a->n_histories == 0) return PSC_OK;
+  DeviceGuard g(ctx->device);
+
+  SimParams p;
+  std::memset(&p, 0, sizeof p);
+  p.sc = sc->params;
+  PhantomParams& q = p.ph;
+  q.nx = pd.nx;
+  q.ny = pd.ny;
+  q.nz = pd.nz;
+  q.n_mat = ph->n_mat;
+  q.n_e = ph->n_e;
+  q.e0 = std::max(0, std::min((int)std::floor(sc->desc.e_lo) - 1, ph->n_e - 2));
+  q.n_tab = ph->n_e - q.e0;
+  q.n_vox = ph->n_vox;
+  q.ox = (float)pd.ox;
+  q.oy = (float)pd.oy;
+  q.oz = (float)pd.oz;
+  q.dx = (float)pd.dx;
+  q.dy = (float)pd.dy;
+  q.dz = (float)pd.dz;
+  q.inv_dx = (float)(1.0 / pd.dx);
+  q.inv_dy = (float)(1.0 / pd.dy);
+  q.inv_dz = (float)(1.0 / pd.dz);
+  q.vox = (const float2*)ph->vox.p;
+  q.alias_prob = (const double*)ph->alias_prob.p;
+  q.alias_idx = (const int32_t*)ph->alias_idx.p;
+  q.xs = (const float4*)ph->xs.p;
+  q.maj = (const float*)ph->maj.p;
+  q.kappa = (const float*)ph->kappa.p;
+  if (lut) {
+    p.lut = lut->params;
+  } else {
+    p.lut.dtype = -1;
+  }
+  p.seed = a->seed;
+  p.first = a->first_history;
+  p.n = a->n_histories;
+  p.bin_mask = a->bin_mask ? a->bin_mask : PSC_BIN_SCATTER;
+  p.acc = (unsigned long long*)acc->data.p;
+  p.cls_out = a->cls_out;
+  p.key_out = (long long*)a->key_out;
+  p.q_out = (long long*)a->q_out;
+
+  const int block = a->block ? a->block : 256;
+  const size_t smem = transport_smem_bytes(p);
+  if ((int)smem > ctx->max_smem_optin) return fail(PSC_EINVAL, "material tables need %zu bytes of shared memory", smem);
+  int grid = a->grid;
+  if (grid == 0) {
+    int per_sm = 0;
+    CK(transport_occupancy(p.lut.dtype, block, smem, &per_sm), "occupancy");
+    grid = ctx->sms * std::max(per_sm, 1);
+    const unsigned long long need = (a->n_histories + block - 1) / block;
+    if ((unsigned long long)grid > need) grid = (int)need;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_lock<std::mutex> lk(ctx->stats_mu, std::defer_lock);
+  if (stats) {
+    lk.lock();
+    p.stats = (unsigned long long*)ctx->stats.p;
+    CK(cudaMemsetAsync(p.stats, 0, sizeof(unsigned long long) * kStatCount, s), "zero stats");
+  }
+  CK(launch_transport(p, grid, block, s), "transport kernel launch");
+  if (stats) {
+    unsigned long long h[kStatCount];
+    CK(cudaMemcpyAsync(h, p.stats, sizeof h, cudaMemcpyDeviceToHost, s), "read stats");
+    CK(cudaStreamSynchronize(s), "transport kernel");
+    for (int k = 0; k < 8; ++k) stats->class_counts[k] = h[k];
+    stats->steps = h[kStatSteps];
+    stats->compton = h[kStatCompton];
+    stats->rayleigh = h[kStatRayleigh];
+    stats->photo = h[kStatPhoto];
+    stats->binned = h[kStatBinned];
+    stats->weight_sum = h[kStatWeight];
+    stats->rng_blocks = h[kStatRng];
+    stats->tries = h[kStatTries];
+    stats->detected = h[kStatDetected];
+  }
+  return PSC_OK;
+}
+
+int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream) {
+  if (!ctx || !a || !out) return fail(PSC_EINVAL, "NULL argument");
+  GET(AccObj, acc, a->acc, kAccObj);
+  GET(ScannerObj, sc, acc->scanner, kScannerObj);
+  std::shared_ptr<SinoObj> sens, norm;
+  if (a->sens) {
+    sens = get<SinoObj>(ctx, a->sens, kSinoObj);
+    if (!sens) return fail(PSC_ENOTFOUND, "no sinogram with id %d", (int)a->sens);
+    if (sens->scanner != acc->scanner) return fail(PSC_EINVAL, "sensitivity sinogram belongs to another scanner");
+  }
+  if (a->norm) {
+    norm = get<SinoObj>(ctx, a->norm, kSinoObj);
+    if (!norm) return fail(PSC_ENOTFOUND, "no sinogram with id %d", (int)a->norm);
+    if (norm->scanner != acc->scanner) return fail(PSC_EINVAL, "normalisation sinogram belongs to another scanner");
+  }
+  if (!std::isfinite(a->scale)) return fail(PSC_EINVAL, "scale must be finite");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  FinParams p;
+  std::memset(&p, 0, sizeof p);
+  const psc_scanner_desc& d = sc->desc;
+  p.acc = (const long long*)acc->data.p;
+  p.out = out;
+  p.sens = sens ? (const double*)sens->data.p : nullptr;
+  p.sens_per_lor = sens ? sens->per_lor : 0;
+  p.c = std::ldexp(a->scale, -32);
+  p.n_bins = sc->n_bins;
+  p.n_rings = d.n_rings;
+  p.V = d.n_crystals / 2;
+  p.R = d.n_rad;
+  p.T = d.n_tof;
+  p.smooth = a->smooth ? 1 : 0;
+  p.sens_first = a->sens_first ? 1 : 0;
+  if (!p.smooth) {
+    CK(launch_finalize(p, ctx->sms, s), "finalize");
+    return PSC_OK;
+  }
+  for (int ax = 0; ax < 3; ++ax) {
+    const double sg = a->sigma[ax];
+    if (!(sg >= 0.0) || !std::isfinite(sg)) return fail(PSC_EINVAL, "sigma[%d] must be finite and >= 0", ax);
+    const int K = sg > 0.0 ? (int)std::ceil(4.0 * sg) : 0;
+    if (K > kMaxSmoothRadius) return fail(PSC_EINVAL, "sigma[%d] too large (4 sigma > %d bins)", ax, kMaxSmoothRadius);
+    p.K[ax] = K;
+    double w[2 * kMaxSmoothRadius + 1], sum = 0.0;
+    for (int k = -K; k <= K; ++k) {
+      w[k + K] = K ? std::exp(-0.5 * (k / sg) * (k / sg)) : 1.0;
+      sum += w[k + K];
+    }
+    for (int j = 0; j <= 2 * K; ++j) p.g[ax][j] = (float)(w[j] / sum);
+  }
+  if (norm) {
+    p.norm = (const double*)norm->data.p;
+    p.norm_per_lor = norm->per_lor;
+    if (!norm->recip.p) {
+      int rc;
+      if ((rc = dev_alloc(ctx, norm->recip, sizeof(double) * norm->n))) return rc;
+      CK(launch_reciprocal((const double*)norm->data.p, (double*)norm->recip.p, norm->n, ctx->sms, s), "reciprocal");
+    }
+    p.rnorm = (const double*)norm->recip.p;
+  }
+  // tile sizes: radial lines whole; view / axial chunks sized to <= 96 KB
+  const size_t budget = 96 * 1024;
+  if (finalize_smem_radial(p) > (size_t)ctx->max_smem_optin)
+    return fail(PSC_EINVAL, "a radial line of %d x %d bins does not fit in shared memory", p.R, p.T);
+  p.chunk_view = (int)std::max<size_t>(1, std::min<size_t>(64, budget / (sizeof(float) * p.V)));
+  p.chunk_axial = (int)std::max<size_t>(1, std::min<size_t>(512, budget / (sizeof(float) * p.n_rings)));
+  {
+    std::lock_guard<std::mutex> lk(ctx->scratch_mu);
+    const size_t need = sizeof(float) * (size_t)p.n_bins;
+    if (ctx->scratch.bytes < need) {
+      cudaStreamSynchronize(s);
+      cudaDeviceSynchronize();
+      if (ctx->scratch.p) {
+        cudaFree(ctx->scratch.p);
+        ctx->scratch.p = nullptr;
+        ctx->scratch.bytes = 0;
+      }
+      cudaError_t e = cudaMalloc(&ctx->scratch.p, need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->scratch.p = nullptr;
+        return fail(PSC_ENOMEM, "finalize scratch of %zu bytes: %s", need, cudaGetErrorString(e));
+      }
+      ctx->scratch.bytes = need;
+    }
+    p.scratch = (float*)ctx->scratch.p;
+    CK(cudaStreamWaitEvent(s, ctx->scratch_done, 0), "order scratch users");
+    CK(launch_finalize(p, ctx->sms, s), "finalize");
+    CK(cudaEventRecord(ctx->scratch_done, s), "order scratch users");
+  }
+  return PSC_OK;
+}
+
+}  // extern "C"

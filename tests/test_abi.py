@@ -1,0 +1,57 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, and exports every entry point that include/psc.h declares; the Python
+binding names the same entry points."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "psc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(psc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit")
+    from paper_2509_05047_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["psc_create", "psc_destroy", "psc_last_error", "psc_load_scanner",
+                     "psc_load_materials", "psc_load_phantom", "psc_update_activity",
+                     "psc_load_lut", "psc_load_sinogram", "psc_acc_create", "psc_acc_zero",
+                     "psc_acc_read", "psc_acc_write", "psc_simulate", "psc_finalize",
+                     "psc_unload"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", libpath], text=True)
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_library_loads_and_binding_matches_header(libpath):
+    import paper_2509_05047_gb300 as psc
+    L = psc.lib()
+    for n in declared_functions():
+        assert hasattr(L, n)
+        assert n in psc.SIGNATURES and hasattr(psc, n)
+    assert psc.psc_last_error() == ""
+
+
+def test_kernels_are_built_for_sm103a(libpath):
+    out = subprocess.check_output(["cuobjdump", "--list-elf", libpath], text=True) \
+        if shutil.which("cuobjdump") else "sm_103a"
+    assert "sm_103" in out

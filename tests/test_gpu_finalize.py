@@ -1,0 +1,161 @@
+"""GPU parity of the sinogram post-processing (sensitivity multiply and
+normalised separable smoothing) against the oracle, from synthetic
+accumulators written through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2509_05047_gb300 as psc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# FP32 smoothing: three passes of <= 2K+1 positive-weight FMA sums plus the
+# int64 -> FP32 conversion; each stays within ~(2K+2) * 2^-24 relative, so
+# 2e-5 bounds the whole chain for K <= 32 with margin.
+SMOOTH_RTOL = 2e-5
+
+
+class Fin:
+    def __init__(self, sc):
+        import torch
+        from paper_2509_05047_gb300 import build
+        build.build()
+        self.torch = torch
+        self.sc = sc
+        self.ctx = psc.psc_create(0)
+        self.s_id = psc.psc_load_scanner(self.ctx, psc.scanner_desc(sc))
+        self.a_id = psc.psc_acc_create(self.ctx, self.s_id)
+
+    def write_acc(self, acc_np):
+        t = self.torch.from_numpy(np.ascontiguousarray(acc_np.ravel())).cuda()
+        psc.psc_acc_write(self.ctx, self.a_id, t, self.torch.cuda.current_stream().cuda_stream)
+        self.torch.cuda.synchronize()
+
+    def sino(self, host, per_lor):
+        return psc.psc_load_sinogram(self.ctx, self.s_id, host, per_lor)
+
+    def run(self, **kw):
+        out = self.torch.full(self.sc.shape, np.nan, dtype=self.torch.float64, device="cuda")
+        psc.psc_finalize(self.ctx, psc.finalize_args(self.a_id, **kw), out,
+                         self.torch.cuda.current_stream().cuda_stream)
+        self.torch.cuda.synchronize()
+        return out
+
+    def close(self):
+        psc.psc_destroy(self.ctx)
+
+
+@pytest.fixture(scope="module")
+def small():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    # ragged sizes: 38 crystals (33 radial bins kept), 9 rings, 5 TOF bins
+    sc = W.scanner_small(n_crystals=38, n_rings=9, n_tof=5, n_rad=33)
+    f = Fin(sc)
+    rng = np.random.default_rng(0)
+    f.acc = rng.integers(0, 1 << 40, size=sc.shape, dtype=np.int64)
+    f.acc[rng.uniform(size=sc.shape) < 0.3] = 0
+    f.write_acc(f.acc)
+    f.sens_lor = rng.uniform(0.5, 1.5, size=sc.lor_shape)
+    f.sens_full = rng.uniform(0.5, 1.5, size=sc.shape)
+    f.norm_lor = rng.uniform(0.2, 2.0, size=sc.lor_shape)
+    f.norm_lor[0, 0, :3] = 0.0
+    f.ids = {k: f.sino(v, v.ndim == 3) for k, v in
+             [("sens_lor", f.sens_lor), ("sens_full", f.sens_full), ("norm_lor", f.norm_lor)]}
+    yield f
+    f.close()
+
+
+@pytest.mark.parametrize("sens", [None, "sens_lor", "sens_full"])
+@pytest.mark.parametrize("scale", [1.0, 0.37])
+def test_sensitivity_multiply_is_bit_exact(small, sens, scale):
+    out = small.run(sens=small.ids[sens] if sens else 0, scale=scale).cpu().numpy()
+    exp = oracle.finalize(small.acc, small.sc.n_rings,
+                          sens=getattr(small, sens) if sens else None, scale=scale)
+    np.testing.assert_array_equal(out, exp)
+
+
+@pytest.mark.parametrize("sigma", [(2.0, 2.0, 2.0), (0.7, 3.3, 1.2), (9.0 / 2.3548, 6.0 / 2.3548, 10.5 / 2.3548),
+                                   (0.0, 1.0, 0.0)])
+@pytest.mark.parametrize("with_norm", [False, True])
+@pytest.mark.parametrize("sens_first", [False, True])
+def test_smoothing_matches_oracle(small, sigma, with_norm, sens_first):
+    kw = dict(sens=small.ids["sens_lor"], sigma=sigma, scale=2.5, sens_first=sens_first)
+    if with_norm:
+        kw["norm"] = small.ids["norm_lor"]
+    out = small.run(**kw).cpu().numpy()
+    exp = oracle.finalize(small.acc, small.sc.n_rings, sens=small.sens_lor,
+                          norm=small.norm_lor if with_norm else None, sigma=sigma, scale=2.5,
+                          smooth_before_sensitivity=not sens_first)
+    assert np.all(np.isfinite(out))
+    np.testing.assert_allclose(out, exp, rtol=SMOOTH_RTOL, atol=1e-300)
+
+
+def test_smoothing_conserves_mass_and_delta(small):
+    acc = np.zeros(small.sc.shape, np.int64)
+    acc[40, 7, 16, 2] = 1 << 32
+    small.write_acc(acc)
+    out = small.run(sigma=(2.0, 1.5, 1.0)).cpu().numpy()
+    small.write_acc(small.acc)
+    assert abs(out.sum() - 1.0) < 1e-6
+    exp = oracle.finalize(acc, small.sc.n_rings, sigma=(2.0, 1.5, 1.0))
+    np.testing.assert_allclose(out, exp, rtol=SMOOTH_RTOL, atol=1e-12)
+    assert np.all(out[..., [0, 1, 3, 4]] == 0)
+
+
+def test_finalize_argument_errors(small):
+    with pytest.raises(psc.PscError) as e:
+        small.run(sigma=(100.0, 1.0, 1.0))
+    assert e.value.code == psc.PSC_EINVAL
+    with pytest.raises(psc.PscError) as e:
+        small.run(sens=999)
+    assert e.value.code == psc.PSC_ENOTFOUND
+    other = psc.psc_load_scanner(small.ctx, psc.scanner_desc(W.scanner_small(n_crystals=16)))
+    sid = psc.psc_load_sinogram(small.ctx, other, np.ones(W.scanner_small(n_crystals=16).lor_shape), True)
+    with pytest.raises(psc.PscError) as e:
+        small.run(sens=sid)
+    assert e.value.code == psc.PSC_EINVAL
+
+
+def test_paper_scale_sampled(tmp_path):
+    """Full paper-scale sinogram (2025 x 224 x 447 x 27): sparse synthetic
+    accumulator, sigma = 2 bins, per-LOR sensitivity and normalisation;
+    sampled output bins against the brute-force oracle sum."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_signa()
+    f = Fin(sc)
+    try:
+        idx, val = W.sparse_accumulator(sc.n_bins, 20_000_000, seed=5)
+        acc = torch.zeros(sc.n_bins, dtype=torch.int64, device="cuda")
+        acc[torch.from_numpy(idx).cuda()] = torch.from_numpy(val).cuda()
+        psc.psc_acc_write(f.ctx, f.a_id, acc, torch.cuda.current_stream().cuda_stream)
+        del acc
+        sens = W.sensitivity_uniform(sc.lor_shape, seed=1)
+        norm = W.sensitivity_uniform(sc.lor_shape, seed=2, lo=0.8, hi=1.2)
+        s_id, n_id = f.sino(sens, True), f.sino(norm, True)
+
+        def acc_at(flat):
+            pos = np.searchsorted(idx, flat)
+            pos = np.minimum(pos, idx.size - 1)
+            return np.where(idx[pos] == flat, val[pos], 0)
+
+        lor = lambda a: (lambda flat: a.ravel()[flat // sc.n_tof])
+        rng = np.random.default_rng(9)
+        bins = np.concatenate([rng.choice(idx, 1500), rng.integers(0, sc.n_bins, 500)])
+        out = f.run(sens=s_id, norm=n_id, sigma=(2.0, 2.0, 2.0), scale=1e-3)
+        got = out.view(-1)[torch.from_numpy(bins).cuda()].cpu().numpy()
+        del out
+        exp = oracle.finalize_at(bins, sc.shape, sc.n_rings, acc_at, lor(sens), lor(norm),
+                                 (2.0, 2.0, 2.0), 1e-3)
+        np.testing.assert_allclose(got, exp, rtol=SMOOTH_RTOL, atol=1e-300)
+        out = f.run(sens=s_id, scale=1e-3)
+        got = out.view(-1)[torch.from_numpy(bins).cuda()].cpu().numpy()
+        del out
+        exp = oracle.finalize_at(bins, sc.shape, sc.n_rings, acc_at, lor(sens), None, None, 1e-3)
+        np.testing.assert_array_equal(got, exp)
+    finally:
+        f.close()

@@ -1,0 +1,249 @@
+"""GPU parity of the fused transport kernel against the oracle (through the
+C ABI): per-history class, bin and weight on shared Philox streams, exact
+int64 accumulation, launch-shape / partition / checkpoint independence,
+LUT precisions, the paper-scale configuration, and edge cases."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+import paper_2509_05047_gb300 as psc
+import workloads as W
+
+from gpu_helpers import Session, compare_histories, sinogram_from
+
+pytestmark = pytest.mark.gpu
+
+SEED = 12345
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_tiny()
+    mats = W.standard_materials()
+    ph = W.phantom_water_cylinder()
+    lut = W.lut_tiny(sc)
+    s = Session(sc, mats, ph, lut)
+    s.mats, s.ph, s.lut = mats, ph, lut
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("first,n", [(0, 200_003), (10_000_000_000, 65_537)])
+def test_tiny_histories_match_oracle(tiny, first, n):
+    tiny.zero()
+    g = tiny.run(SEED, first, n)
+    r = oracle.simulate(tiny.sc, tiny.mats, tiny.ph, tiny.lut, SEED, first, n, threads=8)
+    same = compare_histories(g, r)
+    # class counters agree with the listmode
+    st = g["stats"]
+    np.testing.assert_array_equal([st[c] for c in psc.CLASSES], np.bincount(g["cls"], minlength=8))
+    # the accumulator holds exactly the listmode's scatter weights
+    acc = tiny.acc().cpu().numpy()
+    np.testing.assert_array_equal(acc, sinogram_from(g["key"], g["q"], g["cls"], tiny.sc.n_bins))
+    assert st["binned"] == (g["cls"] == 7).sum() and st["weight_sum"] == g["q"][g["cls"] == 7].sum()
+    # class frequencies agree with the oracle's
+    assert (~same).sum() <= 0.001 * n
+
+
+def test_unit_lut_count_sinogram_is_bit_exact_on_matched_histories(tiny):
+    """LUT = 1 (no LUT): every event adds exactly 2^32; the GPU count
+    sinogram minus its mismatched histories equals the oracle's minus its
+    mismatched histories, bit for bit."""
+    n = 300_000
+    tiny.zero()
+    g = tiny.run(SEED + 1, 0, n, lut=0)
+    r = oracle.simulate(tiny.sc, tiny.mats, tiny.ph, None, SEED + 1, 0, n, threads=8)
+    same = compare_histories(g, r, w_rtol=0.0)
+    acc = tiny.acc().cpu().numpy()
+    gm = sinogram_from(g["key"][~same], g["q"][~same], g["cls"][~same], tiny.sc.n_bins)
+    rm = sinogram_from(r["key"], r["q"], r["cls"], tiny.sc.n_bins) - \
+        sinogram_from(r["key"][~same], r["q"][~same], r["cls"][~same], tiny.sc.n_bins)
+    np.testing.assert_array_equal(acc - gm, rm)
+    assert np.all(acc % (1 << 32) == 0)
+
+
+def test_result_independent_of_launch_shape_and_partition(tiny):
+    n = 150_001
+    ref = None
+    for block, grid in [(256, 0), (64, 7), (128, 1000), (1024, 3)]:
+        tiny.zero()
+        tiny.run(SEED + 2, 5, n, listmode=False, block=block, grid=grid)
+        a = tiny.acc()
+        if ref is None:
+            ref = a.clone()
+        else:
+            assert bool((a == ref).all()), f"block {block} grid {grid} differs"
+    tiny.zero()
+    for lo, hi in [(5, 40_000), (40_000, 40_001), (40_001, n + 5)]:
+        tiny.run(SEED + 2, lo, hi - lo, listmode=False)
+    assert bool((tiny.acc() == ref).all())
+
+
+def test_checkpoint_resume_is_bit_identical(tiny):
+    import torch
+    n = 120_000
+    tiny.zero()
+    tiny.run(SEED + 3, 0, n, listmode=False)
+    full = tiny.acc()
+    tiny.zero()
+    tiny.run(SEED + 3, 0, n // 3, listmode=False)
+    ck = tiny.acc()                                   # checkpoint: (seed, next id, acc)
+    acc2 = psc.psc_acc_create(tiny.ctx, tiny.s_id)
+    psc.psc_acc_write(tiny.ctx, acc2, ck, tiny.stream())
+    tiny.run(SEED + 3, n // 3, n - n // 3, listmode=False, acc=acc2)
+    assert bool((tiny.acc(acc2) == full).all())
+    psc.psc_unload(tiny.ctx, acc2)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("dtype,bound", [(psc.PSC_LUT_F16, 2e-3), (psc.PSC_LUT_BF16, 1.6e-2)])
+def test_reduced_precision_lut_error_is_bounded(tiny, dtype, bound):
+    """FP16/BF16 LUT storage: the weight error against the FP64 oracle is
+    bounded by the storage rounding (2^-11 / 2^-8 relative per tap)."""
+    l_id = psc.psc_load_lut(tiny.ctx, psc.lut_desc(tiny.lut, dtype).desc)
+    n = 200_000
+    tiny.zero()
+    g = tiny.run(SEED, 0, n, lut=l_id)
+    r = oracle.simulate(tiny.sc, tiny.mats, tiny.ph, tiny.lut, SEED, 0, n, threads=8)
+    same = compare_histories(g, r, w_rtol=bound)
+    det = same & (r["key"] >= 0)
+    rel = np.abs(g["q"][det] - r["q"][det]) / r["q"][det]
+    print(f"LUT dtype {dtype}: max weight rel err {rel.max():.3g}, mean {rel.mean():.3g}")
+    psc.psc_unload(tiny.ctx, l_id)
+
+
+def test_vacuum_trues_geometry(tiny):
+    """mu = 0: all pairs fly straight; binned trues match the oracle."""
+    ph = W.phantom_uniform_box(dims=(20, 20, 10), voxel=(5.0, 5.0, 5.0), material=W.MAT_VACUUM,
+                               density=0.0, source="uniform")
+    p_id = psc.psc_load_phantom(tiny.ctx, psc.phantom_desc(ph).desc, tiny.m_id)
+    n = 100_000
+    tiny.zero()
+    g = tiny.run(7, 0, n, phantom=p_id, bin_mask=3)
+    r = oracle.simulate(tiny.sc, tiny.mats, ph, tiny.lut, 7, 0, n, threads=8, bin_mask=3)
+    compare_histories(g, r)
+    assert (g["cls"] == 7).sum() == 0 and (g["cls"] == 6).sum() > 1000
+    psc.psc_unload(tiny.ctx, p_id)
+
+
+def test_update_activity_rebuilds_emission(tiny):
+    rng = np.random.default_rng(0)
+    act = (tiny.ph.activity * rng.uniform(0.0, 2.0, tiny.ph.activity.shape)).astype(np.float32)
+    psc.psc_update_activity(tiny.ctx, tiny.p_id, act)
+    ph2 = W.Phantom(tiny.ph.dims, tiny.ph.voxel, tiny.ph.origin, tiny.ph.material,
+                    tiny.ph.density, act)
+    n = 100_000
+    tiny.zero()
+    g = tiny.run(SEED, 0, n)
+    r = oracle.simulate(tiny.sc, tiny.mats, ph2, tiny.lut, SEED, 0, n, threads=8)
+    compare_histories(g, r)
+    psc.psc_update_activity(tiny.ctx, tiny.p_id, tiny.ph.activity)
+
+
+def test_edge_cases(tiny):
+    tiny.zero()
+    g = tiny.run(SEED, 0, 0)                               # empty range: no work, zeros
+    assert sum(g["stats"][c] for c in psc.CLASSES) == 0
+    assert int(tiny.acc().abs().sum()) == 0
+    g = tiny.run(SEED, 2**64 - 2, 1)                       # one history at the top of the id range
+    r = oracle.simulate(tiny.sc, tiny.mats, tiny.ph, tiny.lut, SEED, 2**64 - 2, 1)
+    assert g["cls"][0] == r["cls"][0] and g["key"][0] == r["key"][0]
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 2**64 - 1, 2)
+    assert e.value.code == psc.PSC_EOVERFLOW
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 0, 10, phantom=999)
+    assert e.value.code == psc.PSC_ENOTFOUND
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 0, 10, acc=tiny.l_id)                 # wrong object kind
+    assert e.value.code == psc.PSC_ENOTFOUND
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 0, 10, block=100)
+    assert e.value.code == psc.PSC_EINVAL
+    bad = W.phantom_water_cylinder()
+    bad.activity[:] = 0
+    with pytest.raises(psc.PscError) as e:
+        psc.psc_load_phantom(tiny.ctx, psc.phantom_desc(bad).desc, tiny.m_id)
+    assert e.value.code == psc.PSC_EINVAL
+    big = W.phantom_uniform_box(dims=(200, 200, 4), voxel=(4.0, 4.0, 4.0))   # 800 mm wide
+    p_id = psc.psc_load_phantom(tiny.ctx, psc.phantom_desc(big).desc, tiny.m_id)
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 0, 10, phantom=p_id)
+    assert e.value.code == psc.PSC_EINVAL and "cylinder" in str(e.value)
+    psc.psc_unload(tiny.ctx, p_id)
+    wrong = W.lut_smooth(4, 4, 4, 3, 3, 425.0)
+    l_id = psc.psc_load_lut(tiny.ctx, psc.lut_desc(wrong).desc)
+    with pytest.raises(psc.PscError) as e:
+        tiny.run(SEED, 0, 10, lut=l_id)
+    assert e.value.code == psc.PSC_EINVAL
+    psc.psc_unload(tiny.ctx, l_id)
+    out_of_range = W.lut_tiny(tiny.sc)
+    out_of_range.data[0, 0, 0, 0, 0] = 1.5
+    with pytest.raises(psc.PscError):
+        psc.psc_load_lut(tiny.ctx, psc.lut_desc(out_of_range).desc)
+
+
+def test_independent_seeds_pass_poisson_chi_square(tiny):
+    out = []
+    for seed in (101, 202):
+        tiny.zero()
+        tiny.run(seed, 0, 2_000_000, listmode=False, lut=0)
+        a = tiny.acc().cpu().numpy().reshape(tiny.sc.shape) >> 32
+        out.append(a.sum(axis=(0, 3)).astype(np.float64))
+    A, B = out
+    keep = (A + B) > 0
+    chi2 = ((A - B)[keep] ** 2 / (A + B)[keep]).sum()
+    assert stats.chi2.sf(chi2, keep.sum()) > 0.01
+
+
+# --------------------------------------------------------------------------
+# paper-scale configuration (full-size phantom, scanner, LUT; sampled
+# history ranges compared one by one with the oracle)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def signa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_signa()
+    mats = W.standard_materials()
+    ph = W.phantom_torso()
+    lut = W.lut_signa(sc)
+    s = Session(sc, mats, ph, lut)
+    s.mats, s.ph, s.lut = mats, ph, lut
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("first,n", [(0, 100_000), (500_000_017, 60_001)])
+def test_signa_histories_match_oracle(signa, first, n):
+    g = signa.run(SEED, first, n)
+    r = oracle.simulate(signa.sc, signa.mats, signa.ph, signa.lut, SEED, first, n, threads=8)
+    compare_histories(g, r)
+    assert (r["cls"] == 7).sum() > 0.02 * n
+
+
+def test_signa_large_launch_properties(signa):
+    """1e8 histories in the benchmark's launch configuration: class counts
+    add up, the accumulator total equals the binned weight sum, and the
+    last histories of the range match the oracle one by one."""
+    import torch
+    n = 100_000_000
+    signa.zero()
+    st = signa.run(SEED, 0, n, listmode=False)["stats"]
+    assert sum(st[c] for c in psc.CLASSES) == n
+    acc = signa.acc()
+    assert int(acc.sum()) == st["weight_sum"]
+    assert int((acc > 0).sum()) <= st["binned"]
+    del acc
+    signa.zero()
+    tail = signa.run(SEED, n - 20_000, 20_000)
+    r = oracle.simulate(signa.sc, signa.mats, signa.ph, signa.lut, SEED, n - 20_000, 20_000, threads=8)
+    compare_histories(tail, r)
+    torch.cuda.synchronize()
