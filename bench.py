@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rings", type=int, default=0,
+                    help="profiling case: keep only this many rings (smaller sinogram)")
+    ap.add_argument("--tof-bins", type=int, default=0,
+                    help="profiling case: this many TOF bins over the same 648 mm range")
     return ap.parse_args()
 
 
@@ -122,8 +126,14 @@ def transport_ops(st):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
-def build_inputs():
+def build_inputs(rings=0, tof_bins=0):
     sc = W.scanner_signa()
+    if rings:
+        sc = W.Scanner(sc.radius, sc.n_crystals, rings, sc.ring_pitch, sc.module_t, sc.module_a,
+                       sc.e_lo, sc.e_hi, sc.n_tof, sc.tof_bin_mm, sc.tof_sigma_mm)
+    if tof_bins:
+        sc.tof_bin_mm = sc.n_tof * sc.tof_bin_mm / tof_bins
+        sc.n_tof = tof_bins
     mats = W.standard_materials()
     ph = W.phantom_torso()
     lut = W.lut_signa(sc)
@@ -146,7 +156,7 @@ def run_native(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    sc, mats, ph, lut, sens = build_inputs()
+    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins)
     n = int(a.histories)
     ctx = psc.psc_create(local)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
@@ -229,10 +239,12 @@ def run_native(a):
                 "unit": "Gop/s", "frac": round(achieved / peak_ops, 4), "traffic": None,
                 "kernel": "psc::transport_kernel<0>", "kernel_ms": round(kern_ms, 3),
                 "peak_source": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    workload = WORKLOAD if not (a.rings or a.tof_bins) else \
+        f"profiling case: {WORKLOAD} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "histories_per_step": n, "global_batch": world * n,
+           "config": {"workload": workload, "histories_per_step": n, "global_batch": world * n,
                       "l2": "inputs larger than L2 (43.8 GB accumulator + 43.8 GB output streamed every step)",
                       "parallelism": f"replicas{world}"},
            "roofline": roofline, "clocks": clocks, "e2e": e2e,

@@ -21,7 +21,9 @@ struct FinParams {
   long long n_bins;
   int n_rings, V, R, T;
   int smooth, sens_first;
-  int chunk_view, chunk_axial;
+  int chunk_view, chunk_axial;          // column chunks (powers of two)
+  int chunk_view_log2, chunk_axial_log2;
+  unsigned magic_T;                     // ceil(2^32 / T) for exact i / T, 0 when T == 1
   int K[3];                    // truncation radius per axis (radial, view, axial)
   float g[3][2 * kMaxSmoothRadius + 1];
 };

@@ -12,6 +12,8 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <tuple>
+#include <utility>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -593,8 +595,8 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
   if (acc->scanner != a->scanner) return fail(PSC_EINVAL, "accumulator belongs to scanner %d", (int)acc->scanner);
   if (a->first_history + a->n_histories < a->first_history) return fail(PSC_EOVERFLOW, "history range wraps");
   if (a->bin_mask < 0 || a->bin_mask > 3) return fail(PSC_EINVAL, "bin_mask must be in [0, 3]");
-  if (a->block < 0 || a->block > 1024 || (a->block % 32) || a->grid < 0)
-    return fail(PSC_EINVAL, "block must be a multiple of 32 in [32, 1024], grid >= 0");
+  if (a->block < 0 || a->block > 256 || (a->block % 32) || a->grid < 0)
+    return fail(PSC_EINVAL, "block must be a multiple of 32 in [32, 256], grid >= 0");
   const psc_phantom_desc& pd = ph->desc;
   const double R2 = sc->desc.radius * sc->desc.radius;
   for (int i = 0; i < 4; ++i) {
@@ -716,6 +718,9 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
   p.T = d.n_tof;
   p.smooth = a->smooth ? 1 : 0;
   p.sens_first = a->sens_first ? 1 : 0;
+  p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
+  if ((long long)p.V * p.R * p.T * p.T >= (1LL << 32))
+    return fail(PSC_EOVERFLOW, "a sinogram plane is too large");
   if (!p.smooth) {
     CK(launch_finalize(p, ctx->sms, s), "finalize");
     return PSC_OK;
@@ -743,12 +748,27 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
     }
     p.rnorm = (const double*)norm->recip.p;
   }
-  // tile sizes: radial lines whole; view / axial chunks sized to <= 96 KB
-  const size_t budget = 96 * 1024;
+  // tile sizes: radial lines whole; view / axial column chunks (powers of
+  // two) sized so a tile stays within 48 KB
+  p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
+  const long long J = (long long)p.V * p.R * p.T;
+  if (J * p.T >= (1LL << 32)) return fail(PSC_EOVERFLOW, "a sinogram plane of %lld bins is too large", J);
   if (finalize_smem_radial(p) > (size_t)ctx->max_smem_optin)
     return fail(PSC_EINVAL, "a radial line of %d x %d bins does not fit in shared memory", p.R, p.T);
-  p.chunk_view = (int)std::max<size_t>(1, std::min<size_t>(64, budget / (sizeof(float) * p.V)));
-  p.chunk_axial = (int)std::max<size_t>(1, std::min<size_t>(512, budget / (sizeof(float) * p.n_rings)));
+  auto pick = [](long long rows, int cap) {
+    int ch = 1, lg = 0;
+    while (ch * 2 <= cap && (long long)(ch * 2) * rows * (long long)sizeof(float) <= 48 * 1024) {
+      ch *= 2;
+      ++lg;
+    }
+    return std::make_pair(ch, lg);
+  };
+  const long long rows_v = (p.V + 7) / 8 * 8 + 2 * p.K[1];
+  const long long rows_a = (p.n_rings + 7) / 8 * 8 + 2 * p.K[2];
+  std::tie(p.chunk_view, p.chunk_view_log2) = pick(rows_v, 32);
+  std::tie(p.chunk_axial, p.chunk_axial_log2) = pick(rows_a, 128);
+  if (finalize_smem_view(p) > (size_t)ctx->max_smem_optin || finalize_smem_axial(p) > (size_t)ctx->max_smem_optin)
+    return fail(PSC_EINVAL, "smoothing tiles do not fit in shared memory");
   {
     std::lock_guard<std::mutex> lk(ctx->scratch_mu);
     const size_t need = sizeof(float) * (size_t)p.n_bins;
