@@ -139,6 +139,7 @@ typedef struct {
   uint64_t rng_blocks;             /* Philox4x32-10 blocks generated */
   uint64_t tries;                  /* Compton and Rayleigh rejection-sampling tries */
   uint64_t detected;               /* photons that reached the detector inside the window */
+  uint64_t atomics;                /* global atomics issued (events of a warp in one bin share one) */
 } psc_stats;
 
 /* Sinogram post-processing (Sec. 2.2.4, 2.3.2). */
@@ -170,6 +171,12 @@ int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* desc, int32_t materia
 /* New activity image for a loaded phantom (joint activity/scatter
  * estimation, Sec. 2.3.3 step 2): rebuilds the alias table only. */
 int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity /* host */);
+/* Copy a phantom's resident emission alias table to host arrays of n_vox
+ * entries: column v is kept when (x >> 9) < threshold[v] for the Philox word
+ * x of the acceptance draw (equivalently u < prob[v] of Vose's table), else
+ * alias[v] is emitted. */
+int psc_phantom_alias(psc_ctx* ctx, int32_t phantom, uint32_t* threshold /* host */,
+                      int32_t* alias /* host */);
 /* Detection-probability LUT (Sec. 2.2.2); data == NULL loads a LUT of ones. */
 int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* desc, int32_t* id);
 /* Sensitivity (Sec. 2.2.4) or smoothing-normalisation (Sec. 2.3.2) sinogram

@@ -74,12 +74,12 @@ class Stats(C.Structure):
     _fields_ = [("class_counts", C.c_uint64 * 8), ("steps", C.c_uint64), ("compton", C.c_uint64),
                 ("rayleigh", C.c_uint64), ("photo", C.c_uint64), ("binned", C.c_uint64),
                 ("weight_sum", C.c_uint64), ("rng_blocks", C.c_uint64), ("tries", C.c_uint64),
-                ("detected", C.c_uint64)]
+                ("detected", C.c_uint64), ("atomics", C.c_uint64)]
 
     def as_dict(self):
         d = {k: int(v) for k, v in zip(CLASSES, self.class_counts)}
         for f in ("steps", "compton", "rayleigh", "photo", "binned", "weight_sum", "rng_blocks",
-                  "tries", "detected"):
+                  "tries", "detected", "atomics"):
             d[f] = int(getattr(self, f))
         return d
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "psc_load_materials": (C.c_int, [_P, C.POINTER(MaterialsDesc), C.POINTER(_I32)]),
     "psc_load_phantom": (C.c_int, [_P, C.POINTER(PhantomDesc), _I32, C.POINTER(_I32)]),
     "psc_update_activity": (C.c_int, [_P, _I32, _P]),
+    "psc_phantom_alias": (C.c_int, [_P, _I32, _P, _P]),
     "psc_load_lut": (C.c_int, [_P, C.POINTER(LutDesc), C.POINTER(_I32)]),
     "psc_load_sinogram": (C.c_int, [_P, _I32, _P, _I32, C.POINTER(_I32)]),
     "psc_acc_create": (C.c_int, [_P, _I32, C.POINTER(_I32)]),
@@ -193,6 +194,13 @@ def psc_load_phantom(ctx, desc: PhantomDesc, materials):
 def psc_update_activity(ctx, phantom, activity):
     a = np.ascontiguousarray(activity, dtype=np.float32)
     _check(lib().psc_update_activity(ctx, phantom, a.ctypes.data))
+
+
+def psc_phantom_alias(ctx, phantom, n_vox):
+    thr = np.zeros(n_vox, dtype=np.uint32)
+    alias = np.zeros(n_vox, dtype=np.int32)
+    _check(lib().psc_phantom_alias(ctx, phantom, thr.ctypes.data, alias.ctypes.data))
+    return thr, alias
 
 
 def psc_load_lut(ctx, desc: LutDesc):

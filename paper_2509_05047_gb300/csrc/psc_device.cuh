@@ -16,6 +16,7 @@ namespace psc {
 constexpr int kMaxMaterials = 8;
 constexpr int kMaxSteps = 4096;     // Woodcock steps per photon (safety bound)
 constexpr int kMaxTries = 64;       // rejection-sampling tries, last proposal kept
+constexpr int kRingWords = 8;       // per-lane window of the current Philox sub-stream
 constexpr float kPolarEps = 1e-6f;  // |d_z| > 1 - eps: rotate about the z axis
 constexpr float kRestKeV = 511.0f;
 constexpr float kEmitKeV = 511.0f;
@@ -30,7 +31,7 @@ enum : int {
 enum : int {
   kStatClass0 = 0, kStatSteps = 8, kStatCompton = 9, kStatRayleigh = 10, kStatPhoto = 11,
   kStatBinned = 12, kStatWeight = 13, kStatRng = 14, kStatTries = 15, kStatDetected = 16,
-  kStatCount = 17
+  kStatAtomics = 17, kStatCount = 18
 };
 
 struct ScannerParams {
@@ -48,8 +49,7 @@ struct PhantomParams {
   long long n_vox;
   float ox, oy, oz, inv_dx, inv_dy, inv_dz, dx, dy, dz;
   const float2* vox;           // {density, material id bits}
-  const double* alias_prob;
-  const int32_t* alias_idx;
+  const uint2* alias;          // per alias column {acceptance threshold on x >> 9, alias voxel}
   const float4* xs;            // [n_mat][n_e] cumulative {C, C+R, C+R+P, 0} (mm^-1 per g/cm^3)
   const float* maj;            // [n_e] Woodcock majorant (mm^-1), rounded up
   const float* kappa;          // [n_mat]
@@ -98,91 +98,10 @@ __device__ __forceinline__ float u01(uint32_t x) {
   return (float)((x >> 9) * 2u + 1u) * 0x1p-24f;
 }
 
-// Sequential uniforms of one history's sub-stream: draw k is word k % 4 of
-// the Philox block with counter (history lo, history hi, k / 4, stream).
-struct Rng {
-  uint2 key;
-  uint32_t h0, h1, stream, block;
-  uint4 buf;
-  int left;
-
-  __device__ __forceinline__ void init(unsigned long long seed, unsigned long long hist, uint32_t s) {
-    key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    h0 = (uint32_t)hist;
-    h1 = (uint32_t)(hist >> 32);
-    stream = s;
-    block = 0;
-    left = 0;
-  }
-  __device__ __forceinline__ float next() {
-    if (left == 0) {
-      buf = philox4x32_10(make_uint4(h0, h1, block, stream), key);
-      ++block;
-      left = 4;
-    }
-    const uint32_t x = buf.x;
-    buf.x = buf.y;
-    buf.y = buf.z;
-    buf.z = buf.w;
-    --left;
-    return u01(x);
-  }
-};
-
 __device__ __forceinline__ uint4 philox_block(unsigned long long seed, unsigned long long hist,
                                               uint32_t block, uint32_t stream) {
   return philox4x32_10(make_uint4((uint32_t)hist, (uint32_t)(hist >> 32), block, stream),
                        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-}
-
-// ---------------------------------------------------------------------------
-// Interaction sampling
-// ---------------------------------------------------------------------------
-
-// Klein-Nishina by Kahn's rejection method on x = E/E' in [1, 1 + 2a]:
-// branch A (probability (1+2a)/(9+2a)): x uniform, accept 4(x-1)/x^2;
-// branch B: x ~ 1/x^2, accept (cos^2 + 1/x)/2.
-__device__ __forceinline__ int sample_compton(Rng& r, float e, float& x, float& c) {
-  const float a = e / kRestKeV;
-  const float two_a = 2.0f * a;
-  const float p_a = (1.0f + two_a) / (9.0f + two_a);
-  x = 1.0f;
-  c = 1.0f;
-  int t = 0;
-  while (t < kMaxTries) {
-    ++t;
-    const float r1 = r.next(), r2 = r.next(), r3 = r.next();
-    bool accept;
-    if (r1 < p_a) {
-      x = 1.0f + two_a * r2;
-      c = 1.0f - (x - 1.0f) / a;
-      accept = r3 < 4.0f * (1.0f / x - 1.0f / (x * x));
-    } else {
-      x = (1.0f + two_a) / (1.0f + two_a * r2);
-      c = 1.0f - (x - 1.0f) / a;
-      accept = r3 < 0.5f * (c * c + 1.0f / x);
-    }
-    if (accept) break;
-  }
-  return t;
-}
-
-// Rayleigh: s = (1 - cos)/2 from (1 + b s)^-2 by inversion, accepted with
-// the Thomson factor (1 + cos^2)/2; b = kappa (E/511)^2.
-__device__ __forceinline__ float sample_rayleigh(Rng& r, float e, float kappa, int& tries) {
-  const float er = e / kRestKeV;
-  const float b = kappa * er * er;
-  float c = 1.0f;
-  int t = 0;
-  while (t < kMaxTries) {
-    ++t;
-    const float u1 = r.next(), u2 = r.next();
-    const float s = u1 / (1.0f + b * (1.0f - u1));
-    c = 1.0f - 2.0f * s;
-    if (u2 < 0.5f * (1.0f + c * c)) break;
-  }
-  tries = t;
-  return c;
 }
 
 // direction after scattering by polar cosine c and azimuth 2 pi u
@@ -200,43 +119,6 @@ __device__ __forceinline__ void rotate(float3& d, float c, float u) {
   const float ny = c * d.y + sn * (cp * d.y * d.z + sp * d.x) / rr;
   const float nz = c * d.z - sn * cp * rr;
   d = make_float3(nx, ny, nz);
-}
-
-// ---------------------------------------------------------------------------
-// Detection on the cylinder
-// ---------------------------------------------------------------------------
-struct Hit {
-  int status, crystal, ring;
-  float alpha, beta, dist;   // degrees, mm
-};
-
-__device__ __forceinline__ Hit detect(const ScannerParams& S, float3 p, float3 d, float e) {
-  Hit h;
-  h.crystal = 0;
-  h.ring = 0;
-  h.alpha = 0.0f;
-  h.beta = 0.0f;
-  h.dist = 0.0f;
-  const float a = d.x * d.x + d.y * d.y;
-  if (!(a > 0.0f)) { h.status = kLostAxial; return h; }
-  const float b = p.x * d.x + p.y * d.y;
-  const float c = p.x * p.x + p.y * p.y - S.r2;
-  const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
-  const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
-  const float hx = p.x + t * d.x, hy = p.y + t * d.y, hz = p.z + t * d.z;
-  h.dist = t;
-  if (!(hz >= -S.half_len && hz < S.half_len)) { h.status = kLostAxial; return h; }
-  h.ring = max(0, min((int)floorf((hz + S.half_len) * S.inv_pitch), S.n_rings - 1));
-  float phi = atan2f(hy, hx);
-  if (phi < 0.0f) phi += 6.283185307179586f;
-  h.crystal = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
-  const float nx = hx / S.radius, ny = hy / S.radius;
-  const float dn = d.x * nx + d.y * ny;
-  const float dt = -d.x * ny + d.y * nx;
-  h.alpha = atan2f(dt, dn) * 57.29577951308232f;
-  h.beta = atan2f(d.z, dn) * 57.29577951308232f;
-  h.status = (e < S.e_lo || e > S.e_hi) ? kEnergyWindow : kDetected;
-  return h;
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ struct FinParams {
   float g[3][2 * kMaxSmoothRadius + 1];
 };
 
-size_t transport_smem_bytes(const SimParams& p);
+size_t transport_smem_bytes(const SimParams& p, int block);
 cudaError_t launch_transport(const SimParams& p, int grid, int block, cudaStream_t s);
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm);
 

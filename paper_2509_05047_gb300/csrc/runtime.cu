@@ -1,7 +1,7 @@
 // runtime.cu -- host runtime and C ABI of libpsc (declared in include/psc.h).
 //
 // A context owns one device's resident state: scanners, material tables,
-// phantoms (packed voxels, FP64 alias table, per-phantom Woodcock majorant),
+// phantoms (packed voxels, alias table, per-phantom Woodcock majorant),
 // LUTs, sensitivity / normalisation sinograms and int64 accumulators.  Calls
 // validate their arguments, never throw across the ABI, and enqueue kernels
 // on the caller's stream.
@@ -81,7 +81,7 @@ struct PhantomObj : Object {
   psc_phantom_desc desc;  // host pointers cleared
   int n_mat = 0, n_e = 0;
   long long n_vox = 0;
-  DevBuf vox, alias_prob, alias_idx, xs, maj, kappa;
+  DevBuf vox, alias, xs, maj, kappa;
   PhantomObj() : Object(kPhantomObj) {}
 };
 
@@ -370,13 +370,23 @@ int psc_load_materials(psc_ctx* ctx, const psc_materials_desc* d, int32_t* id) {
   return PSC_OK;
 }
 
+// Alias acceptance as an integer threshold: a uniform u = (2k + 1) 2^-24,
+// k = x >> 9, satisfies u < p exactly when k < ceil((p 2^24 - 1) / 2), so the
+// kernel decides with one integer compare what the FP64 comparison decides.
+static uint32_t alias_threshold(double p) {
+  const double t = std::ceil((std::ldexp(p, 24) - 1.0) / 2.0);
+  if (!(t > 0.0)) return 0u;
+  return t >= 8388608.0 ? 8388608u : (uint32_t)t;
+}
+
 static int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
   std::vector<double> prob;
   std::vector<int32_t> alias;
   int rc = build_alias(activity, o->n_vox, prob, alias);
   if (rc) return rc;
-  CK(cudaMemcpy(o->alias_prob.p, prob.data(), sizeof(double) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
-  CK(cudaMemcpy(o->alias_idx.p, alias.data(), sizeof(int32_t) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
+  std::vector<uint2> tab((size_t)o->n_vox);
+  for (long long i = 0; i < o->n_vox; ++i) tab[i] = make_uint2(alias_threshold(prob[i]), (uint32_t)alias[i]);
+  CK(cudaMemcpy(o->alias.p, tab.data(), sizeof(uint2) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
   (void)ctx;
   return PSC_OK;
 }
@@ -435,12 +445,11 @@ int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* d, int32_t materials,
   for (int m = 0; m < mat->n_mat; ++m) kap[m] = (float)mat->kappa[m];
   int rc;
   if ((rc = dev_alloc(ctx, o->vox, sizeof(float2) * nv))) return rc;
-  if ((rc = dev_alloc(ctx, o->alias_prob, sizeof(double) * nv))) return rc;
-  if ((rc = dev_alloc(ctx, o->alias_idx, sizeof(int32_t) * nv))) return rc;
+  if ((rc = dev_alloc(ctx, o->alias, sizeof(uint2) * nv))) return rc;
   if ((rc = dev_alloc(ctx, o->xs, sizeof(float4) * xs.size()))) return rc;
   if ((rc = dev_alloc(ctx, o->maj, sizeof(float) * ne))) return rc;
   if ((rc = dev_alloc(ctx, o->kappa, sizeof(float) * kMaxMaterials))) return rc;
-  o->bytes = o->vox.bytes + o->alias_prob.bytes + o->alias_idx.bytes + o->xs.bytes + o->maj.bytes + o->kappa.bytes;
+  o->bytes = o->vox.bytes + o->alias.bytes + o->xs.bytes + o->maj.bytes + o->kappa.bytes;
   CK(cudaMemcpy(o->vox.p, vox.data(), sizeof(float2) * nv, cudaMemcpyHostToDevice), "upload voxels");
   CK(cudaMemcpy(o->xs.p, xs.data(), sizeof(float4) * xs.size(), cudaMemcpyHostToDevice), "upload tables");
   CK(cudaMemcpy(o->maj.p, maj.data(), sizeof(float) * ne, cudaMemcpyHostToDevice), "upload majorant");
@@ -456,6 +465,19 @@ int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity) {
   DeviceGuard g(ctx->device);
   CK(cudaDeviceSynchronize(), "synchronize before activity update");
   return upload_alias(ctx, ph.get(), activity);
+}
+
+int psc_phantom_alias(psc_ctx* ctx, int32_t phantom, uint32_t* threshold, int32_t* alias) {
+  if (!ctx || !threshold || !alias) return fail(PSC_EINVAL, "NULL argument");
+  GET(PhantomObj, ph, phantom, kPhantomObj);
+  DeviceGuard g(ctx->device);
+  std::vector<uint2> tab((size_t)ph->n_vox);
+  CK(cudaMemcpy(tab.data(), ph->alias.p, sizeof(uint2) * ph->n_vox, cudaMemcpyDeviceToHost), "read alias");
+  for (long long i = 0; i < ph->n_vox; ++i) {
+    threshold[i] = tab[i].x;
+    alias[i] = (int32_t)tab[i].y;
+  }
+  return PSC_OK;
 }
 
 int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* d, int32_t* id) {
@@ -629,8 +651,7 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
   q.inv_dy = (float)(1.0 / pd.dy);
   q.inv_dz = (float)(1.0 / pd.dz);
   q.vox = (const float2*)ph->vox.p;
-  q.alias_prob = (const double*)ph->alias_prob.p;
-  q.alias_idx = (const int32_t*)ph->alias_idx.p;
+  q.alias = (const uint2*)ph->alias.p;
   q.xs = (const float4*)ph->xs.p;
   q.maj = (const float*)ph->maj.p;
   q.kappa = (const float*)ph->kappa.p;
@@ -649,7 +670,7 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
   p.q_out = (long long*)a->q_out;
 
   const int block = a->block ? a->block : 256;
-  const size_t smem = transport_smem_bytes(p);
+  const size_t smem = transport_smem_bytes(p, block);
   if ((int)smem > ctx->max_smem_optin) return fail(PSC_EINVAL, "material tables need %zu bytes of shared memory", smem);
   int grid = a->grid;
   if (grid == 0) {
@@ -681,6 +702,7 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
     stats->rng_blocks = h[kStatRng];
     stats->tries = h[kStatTries];
     stats->detected = h[kStatDetected];
+    stats->atomics = h[kStatAtomics];
   }
   return PSC_OK;
 }

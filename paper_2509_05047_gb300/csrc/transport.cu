@@ -2,29 +2,32 @@
 // weight -> LOR/TOF binning kernel (Sec. 2.2.1-2.2.3 of the paper; the
 // simulator itself is the project's own design).
 //
-// One thread owns one history at a time (grid-stride over the history
-// range).  Material cross sections and the Woodcock majorant are staged in
-// shared memory; voxels, alias table and LUT are read through the read-only
-// path from L2.  A history either adds one fixed-point weight to the int64
-// accumulator or nothing (Sec. 2.2.3: events are weighted or discarded,
-// never duplicated).  Integer atomics make the sinogram independent of
-// launch shape and history order.
+// Each lane runs a small state machine over its histories:
+//
+//   EMIT -> STEP <-> {COMPTON, RAYLEIGH} -> ESCAPE -> (photon B) STEP ...
+//        -> ESCAPE -> COINC -> EMIT (next history)
+//
+// and every loop iteration executes each section once, for all lanes in
+// that state together.  Lanes of a warp therefore stay converged on the hot
+// section (one Woodcock step per iteration), and the code holds a single
+// copy of each section, so the instruction cache is not thrashed by inlined
+// copies of the photon loop.  One rejection-sampling try runs per iteration.
+//
+// Random numbers: a history's sub-streams (0: emission + TOF blur, 1: photon
+// A, 2: photon B) are read through an 8-word per-lane window in shared
+// memory; the only Philox4x32-10 evaluation sits at the top of the loop and
+// appends one block when the lane's next section needs more words than the
+// window holds.  The words consumed, and their order, are those of the
+// per-history definition, so results do not depend on the schedule.
+//
+// A history adds one fixed-point weight to the int64 accumulator or nothing
+// (Sec. 2.2.3: weighted or discarded, never duplicated); lanes of a warp
+// that hit the same bin combine their weights before one atomic.
 #include "psc_internal.h"
 
 namespace psc {
 
-struct Photon {
-  float3 pos, dir;
-  float e, path;
-  int n_c, n_r, n_steps;
-  Hit hit;
-};
-
-struct Counters {
-  unsigned int cls[8];
-  unsigned int steps, compton, rayleigh, photo, binned, rng, tries, detected;
-  unsigned long long weight;
-};
+enum : int { kEmit = 0, kStep = 1, kCompton = 2, kRayleigh = 3, kEscape = 4, kCoinc = 5, kDone = 6 };
 
 __device__ __forceinline__ float interp_scalar(const float* t, int n_tab, int e0, float e) {
   const float fe = e - (float)e0;
@@ -40,67 +43,6 @@ __device__ __forceinline__ float4 interp_xs(const float4* t, int n_tab, int e0, 
   const float f = fe - (float)i;
   const float4 a = t[i], b = t[i + 1];
   return make_float4(a.x + f * (b.x - a.x), a.y + f * (b.y - a.y), a.z + f * (b.z - a.z), 0.0f);
-}
-
-// Woodcock delta tracking of one photon, then detection.
-__device__ __forceinline__ void track(const SimParams& P, const float4* s_xs, const float* s_maj,
-                                      const float* s_kappa, Rng& rng, Photon& p, Counters& cnt) {
-  const PhantomParams& ph = P.ph;
-  for (;;) {
-    if (p.n_steps >= kMaxSteps) {
-      p.hit.status = kStepLimit;
-      return;
-    }
-    const float mu_max = interp_scalar(s_maj, ph.n_tab, ph.e0, p.e);
-    if (!(mu_max > 0.0f)) break;
-    const float dist = -logf(rng.next()) / mu_max;
-    const float qx = p.pos.x + dist * p.dir.x;
-    const float qy = p.pos.y + dist * p.dir.y;
-    const float qz = p.pos.z + dist * p.dir.z;
-    const float fx = (qx - ph.ox) * ph.inv_dx;
-    const float fy = (qy - ph.oy) * ph.inv_dy;
-    const float fz = (qz - ph.oz) * ph.inv_dz;
-    if (!(fx >= 0.0f && fx < (float)ph.nx && fy >= 0.0f && fy < (float)ph.ny && fz >= 0.0f &&
-          fz < (float)ph.nz))
-      break;  // outside the grid is vacuum: straight to the detector
-    const int ix = min((int)fx, ph.nx - 1);
-    const int iy = min((int)fy, ph.ny - 1);
-    const int iz = min((int)fz, ph.nz - 1);
-    p.pos = make_float3(qx, qy, qz);
-    p.path += dist;
-    ++p.n_steps;
-    ++cnt.steps;
-    const float2 vx = __ldg(ph.vox + ((long long)iz * ph.ny + iy) * ph.nx + ix);
-    const float rho = vx.x;
-    const int m = __float_as_int(vx.y);
-    const float4 cum = interp_xs(s_xs + m * ph.n_tab, ph.n_tab, ph.e0, p.e);
-    const float t = rng.next() * mu_max;
-    if (t < rho * cum.x) {  // Compton
-      float x, c;
-      cnt.tries += sample_compton(rng, p.e, x, c);
-      rotate(p.dir, c, rng.next());
-      p.e = p.e / x;
-      ++p.n_c;
-      ++cnt.compton;
-      if (p.e < P.sc.e_lo) {
-        p.hit.status = kEnergyWindow;
-        return;
-      }
-    } else if (t < rho * cum.y) {  // Rayleigh
-      int tries;
-      const float c = sample_rayleigh(rng, p.e, s_kappa[m], tries);
-      cnt.tries += tries;
-      rotate(p.dir, c, rng.next());
-      ++p.n_r;
-      ++cnt.rayleigh;
-    } else if (t < rho * cum.z) {  // photo-absorption
-      ++cnt.photo;
-      p.hit.status = kAbsorbed;
-      return;
-    }  // else virtual collision
-  }
-  p.hit = detect(P.sc, p.pos, p.dir, p.e);
-  p.path += p.hit.dist;
 }
 
 __device__ __forceinline__ long long bin_key(const ScannerParams& S, int ca, int cb, int ra, int rb,
@@ -120,93 +62,32 @@ __device__ __forceinline__ long long bin_key(const ScannerParams& S, int ca, int
   return (((long long)plane * S.n_views + view) * S.n_rad + r) * S.n_tof + (int)g;
 }
 
-template <int DT>
-__device__ __forceinline__ void run_history(const SimParams& P, const float4* s_xs,
-                                            const float* s_maj, const float* s_kappa,
-                                            unsigned long long h, Counters& cnt, int& cls,
-                                            long long& key, long long& q) {
-  const PhantomParams& ph = P.ph;
-  key = -1;
-  q = 0;
-  // emission (stream 0, blocks 0 and 1)
-  const uint4 b0 = philox_block(P.seed, h, 0, 0);
-  const uint4 b1 = philox_block(P.seed, h, 1, 0);
-  const long long col = (long long)(((unsigned long long)b0.x * (unsigned long long)ph.n_vox) >> 32);
-  const double pr = __ldg(ph.alias_prob + col);
-  const int v = ((double)u01(b0.y) < pr) ? (int)col : __ldg(ph.alias_idx + col);
-  const int ix = v % ph.nx, iy = (v / ph.nx) % ph.ny, iz = v / (ph.nx * ph.ny);
-  const float3 e0 = make_float3(ph.ox + ((float)ix + u01(b0.z)) * ph.dx,
-                                ph.oy + ((float)iy + u01(b0.w)) * ph.dy,
-                                ph.oz + ((float)iz + u01(b1.x)) * ph.dz);
-  const float ct = 2.0f * u01(b1.y) - 1.0f;
-  float sp, cp;
-  sincospif(2.0f * u01(b1.z), &sp, &cp);
-  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-  const float3 d = make_float3(st * cp, st * sp, ct);
-
-  Photon A, B;
-  A.pos = e0;
-  A.dir = d;
-  A.e = kEmitKeV;
-  A.path = 0.0f;
-  A.n_c = A.n_r = A.n_steps = 0;
-  Rng rng;
-  rng.init(P.seed, h, 1);
-  track(P, s_xs, s_maj, s_kappa, rng, A, cnt);
-  cnt.rng += 2 + rng.block;
-  if (A.hit.status != kDetected) {
-    cls = A.hit.status;
-    return;
-  }
-  B.pos = e0;
-  B.dir = make_float3(-d.x, -d.y, -d.z);
-  B.e = kEmitKeV;
-  B.path = 0.0f;
-  B.n_c = B.n_r = B.n_steps = 0;
-  rng.init(P.seed, h, 2);
-  ++cnt.detected;  // photon A
-  track(P, s_xs, s_maj, s_kappa, rng, B, cnt);
-  cnt.rng += rng.block;
-  if (B.hit.status != kDetected) {
-    cls = B.hit.status;
-    return;
-  }
-  ++cnt.detected;  // photon B
-  if (A.hit.crystal == B.hit.crystal) {
-    cls = kSameCrystal;
-    return;
-  }
-  const bool a_first = A.hit.crystal < B.hit.crystal;
-  const Photon& pa = a_first ? A : B;
-  const Photon& pb = a_first ? B : A;
-  float delta = 0.5f * (pa.path - pb.path);
-  if (P.sc.tof_sigma > 0.0f) {  // Gaussian TOF blur (stream 0, block 2), Box-Muller
-    const uint4 b2 = philox_block(P.seed, h, 2, 0);
-    ++cnt.rng;
-    const float g = sqrtf(-2.0f * logf(u01(b2.x))) * cospif(2.0f * u01(b2.y));
-    delta += P.sc.tof_sigma * g;
-  }
-  key = bin_key(P.sc, pa.hit.crystal, pb.hit.crystal, pa.hit.ring, pb.hit.ring, delta);
-  if (key < 0) {
-    cls = kOutOfRange;
-    return;
-  }
-  const bool scattered = (A.n_c + A.n_r + B.n_c + B.n_r) > 0;
-  cls = scattered ? kScatter : kTrue;
-  const bool take = scattered ? (P.bin_mask & 1) : (P.bin_mask & 2);
-  if (!take && P.q_out == nullptr) return;
-  const float w =
-      lut_prob<DT>(P.lut, A.e, A.hit.alpha, A.hit.beta,
-                   A.hit.crystal % P.sc.module_t, A.hit.ring % P.sc.module_a) *
-      lut_prob<DT>(P.lut, B.e, B.hit.alpha, B.hit.beta, B.hit.crystal % P.sc.module_t,
-                   B.hit.ring % P.sc.module_a);
-  q = __float2ll_rn(w * 4294967296.0f);
-  if (take) {
-    atomicAdd(P.acc + key, (unsigned long long)q);
-    ++cnt.binned;
-    cnt.weight += (unsigned long long)q;
-  }
+// incidence angles (degrees) of direction d at the hit with radial unit
+// vector (nx, ny): transaxial atan2(d.t, d.n), axial atan2(d_z, d.n)
+__device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alpha, float& beta) {
+  const float dn = d.x * nx + d.y * ny;
+  const float dt = -d.x * ny + d.y * nx;
+  alpha = atan2f(dt, dn) * 57.29577951308232f;
+  beta = atan2f(d.z, dn) * 57.29577951308232f;
 }
+
+struct Lane {
+  unsigned long long h;    // current history id
+  unsigned long long m;    // index of the lane's current history within its share
+  int state, photon, tries;
+  uint32_t stream, k, nb;  // sub-stream, next word, blocks generated
+  float3 pos, dir;
+  float e, path;
+  int nint, nsteps;
+  float3 e0, d0;           // emission point and photon A's initial direction
+  // photon A at the detector
+  int a_cr, a_rg, a_scat;
+  float a_e, a_path, a_nx, a_ny;
+  float3 a_dir;
+  // photon B at the detector (set by ESCAPE, used by COINC)
+  int b_cr, b_rg;
+  float b_nx, b_ny;
+};
 
 template <int DT>
 __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ SimParams P) {
@@ -215,59 +96,334 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
   float4* s_xs = smem;
   float* s_maj = reinterpret_cast<float*>(smem + n_xs);
   float* s_kappa = s_maj + P.ph.n_tab;
+  uint32_t* ring = reinterpret_cast<uint32_t*>(s_kappa + kMaxMaterials);  // [kRingWords][blockDim]
+  __shared__ unsigned long long s_cnt[kStatCount];
   for (int i = threadIdx.x; i < n_xs; i += blockDim.x) {
-    const int m = i / P.ph.n_tab, k = i - m * P.ph.n_tab;
-    s_xs[i] = P.ph.xs[m * P.ph.n_e + P.ph.e0 + k];
+    const int mm = i / P.ph.n_tab, kk = i - mm * P.ph.n_tab;
+    s_xs[i] = P.ph.xs[mm * P.ph.n_e + P.ph.e0 + kk];
   }
   for (int i = threadIdx.x; i < P.ph.n_tab; i += blockDim.x) s_maj[i] = P.ph.maj[P.ph.e0 + i];
   if (threadIdx.x < kMaxMaterials)
     s_kappa[threadIdx.x] = threadIdx.x < P.ph.n_mat ? P.ph.kappa[threadIdx.x] : 0.0f;
+  for (int i = threadIdx.x; i < kStatCount; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
 
-  Counters cnt = {};
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
-       i += stride) {
-    int cls;
-    long long key, q;
-    run_history<DT>(P, s_xs, s_maj, s_kappa, P.first + i, cnt, cls, key, q);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) cnt.cls[k] += (cls == k) ? 1u : 0u;
+  const PhantomParams& ph = P.ph;
+  const ScannerParams& S = P.sc;
+  const unsigned tid = threadIdx.x, bdim = blockDim.x;
+  const unsigned lane_id = tid & 31u;
+  const bool stats = P.stats != nullptr;
+  const unsigned long long gtid = (unsigned long long)blockIdx.x * bdim + tid;
+  const unsigned long long nthreads = (unsigned long long)gridDim.x * bdim;
+  const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+  const bool blur = S.tof_sigma > 0.0f;
+
+  auto word = [&](uint32_t w) -> uint32_t { return ring[(w & (kRingWords - 1)) * bdim + tid]; };
+  auto uni = [&](uint32_t w) -> float { return u01(word(w)); };
+  // warp-aggregated counter increment (lanes of the calling branch)
+  auto count = [&](bool pred, int slot) {
+    if (!stats) return;
+    const unsigned act = __activemask();
+    const unsigned b = __ballot_sync(act, pred);
+    if (b && lane_id == (unsigned)(__ffs(act) - 1)) atomicAdd(&s_cnt[slot], (unsigned long long)__popc(b));
+  };
+
+  Lane L;
+  L.m = 0;
+  L.h = P.first + gtid;
+  L.state = gtid < P.n ? kEmit : kDone;
+  L.stream = 0;
+  L.k = 0;
+  L.nb = 0;
+
+  // a history ends: record its class and move to the lane's next history
+  auto finish = [&](int cls, long long key_out, long long q_out) {
+    const unsigned long long i = L.h - P.first;
     if (P.cls_out) P.cls_out[i] = (int8_t)cls;
-    if (P.key_out) P.key_out[i] = key;
-    if (P.q_out) P.q_out[i] = q;
+    if (P.key_out) P.key_out[i] = key_out;
+    if (P.q_out) P.q_out[i] = q_out;
+    if (stats) atomicAdd(&s_cnt[kStatClass0 + cls], 1ull);
+    ++L.m;
+    const unsigned long long idx = gtid + L.m * nthreads;
+    if (idx < P.n) {
+      L.h = P.first + idx;
+      L.state = kEmit;
+      L.stream = 0;
+      L.k = 0;
+      L.nb = 0;
+    } else {
+      L.state = kDone;
+    }
+  };
+
+  while (__any_sync(0xffffffffu, L.state != kDone)) {
+    // words the lane's next section reads from the window
+    const int need = L.state == kEmit ? 7 : L.state == kStep ? 2 : L.state == kCompton ? 4
+                   : L.state == kRayleigh ? 3 : (L.state == kCoinc && blur) ? 2 : 0;
+    // ---- refill: the single Philox evaluation of the loop ----
+    if (need && L.k + need > 4 * L.nb) {
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)L.h, (uint32_t)(L.h >> 32), L.nb, L.stream), key);
+      const uint32_t w0 = 4 * L.nb;
+      ring[((w0 + 0) & (kRingWords - 1)) * bdim + tid] = b.x;
+      ring[((w0 + 1) & (kRingWords - 1)) * bdim + tid] = b.y;
+      ring[((w0 + 2) & (kRingWords - 1)) * bdim + tid] = b.z;
+      ring[((w0 + 3) & (kRingWords - 1)) * bdim + tid] = b.w;
+      ++L.nb;
+      count(true, kStatRng);
+    }
+    // a section runs only when the words it reads are in the window (a lane
+    // can pass through several sections in one iteration)
+    auto avail = [&](uint32_t n) { return L.k + n <= 4 * L.nb; };
+
+    // ---- emission (stream 0, words 0..6) ----
+    if (L.state == kEmit && avail(7)) {
+      const uint32_t w0 = word(0), w1 = word(1);
+      const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
+      const uint2 at = __ldg(ph.alias + col);
+      const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
+      const int ix = v % ph.nx, iy = (v / ph.nx) % ph.ny, iz = v / (ph.nx * ph.ny);
+      L.e0 = make_float3(ph.ox + ((float)ix + uni(2)) * ph.dx, ph.oy + ((float)iy + uni(3)) * ph.dy,
+                         ph.oz + ((float)iz + uni(4)) * ph.dz);
+      const float ct = 2.0f * uni(5) - 1.0f;
+      float sp, cp;
+      sincospif(2.0f * uni(6), &sp, &cp);
+      const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+      L.d0 = make_float3(st * cp, st * sp, ct);
+      L.pos = L.e0;
+      L.dir = L.d0;
+      L.e = kEmitKeV;
+      L.path = 0.0f;
+      L.nint = 0;
+      L.nsteps = 0;
+      L.photon = 0;
+      L.stream = 1;
+      L.k = 0;
+      L.nb = 0;
+      L.state = kStep;
+    }
+
+    // ---- one Woodcock step ----
+    if (L.state == kStep && avail(2)) {
+      bool moved = false;
+      if (L.nsteps >= kMaxSteps) {
+        finish(kStepLimit, -1, 0);
+      } else {
+        const float mu_max = interp_scalar(s_maj, ph.n_tab, ph.e0, L.e);
+        if (!(mu_max > 0.0f)) {
+          L.state = kEscape;
+        } else {
+          const float dist = -__logf(uni(L.k)) / mu_max;
+          ++L.k;
+          const float qx = L.pos.x + dist * L.dir.x;
+          const float qy = L.pos.y + dist * L.dir.y;
+          const float qz = L.pos.z + dist * L.dir.z;
+          const float fx = (qx - ph.ox) * ph.inv_dx;
+          const float fy = (qy - ph.oy) * ph.inv_dy;
+          const float fz = (qz - ph.oz) * ph.inv_dz;
+          if (!(fx >= 0.0f && fx < (float)ph.nx && fy >= 0.0f && fy < (float)ph.ny && fz >= 0.0f &&
+                fz < (float)ph.nz)) {
+            L.state = kEscape;  // outside the grid is vacuum: straight to the detector
+          } else {
+            moved = true;
+            const int ix = min((int)fx, ph.nx - 1);
+            const int iy = min((int)fy, ph.ny - 1);
+            const int iz = min((int)fz, ph.nz - 1);
+            L.pos = make_float3(qx, qy, qz);
+            L.path += dist;
+            ++L.nsteps;
+            const float2 vx = __ldg(ph.vox + ((long long)iz * ph.ny + iy) * ph.nx + ix);
+            const int mat = __float_as_int(vx.y);
+            const float4 cum = interp_xs(s_xs + mat * ph.n_tab, ph.n_tab, ph.e0, L.e);
+            const float t = uni(L.k) * mu_max;
+            ++L.k;
+            if (t < vx.x * cum.x) {
+              L.state = kCompton;
+              L.tries = 0;
+            } else if (t < vx.x * cum.y) {
+              L.state = kRayleigh;
+              L.tries = mat << 16;  // the material id travels with the pending event
+            } else if (t < vx.x * cum.z) {
+              count(true, kStatPhoto);
+              finish(kAbsorbed, -1, 0);
+            }
+          }
+        }
+      }
+      count(moved, kStatSteps);
+    }
+
+    // ---- one Klein-Nishina try (Kahn's method on x = E/E') ----
+    if (L.state == kCompton && avail(4)) {
+      const float r1 = uni(L.k), r2 = uni(L.k + 1), r3 = uni(L.k + 2);
+      L.k += 3;
+      ++L.tries;
+      const float a = L.e / kRestKeV;
+      const float two_a = 2.0f * a;
+      float x, c;
+      bool accept;
+      if (r1 < (1.0f + two_a) / (9.0f + two_a)) {
+        x = 1.0f + two_a * r2;
+        c = 1.0f - (x - 1.0f) / a;
+        accept = r3 < 4.0f * (1.0f / x - 1.0f / (x * x));
+      } else {
+        x = (1.0f + two_a) / (1.0f + two_a * r2);
+        c = 1.0f - (x - 1.0f) / a;
+        accept = r3 < 0.5f * (c * c + 1.0f / x);
+      }
+      count(true, kStatTries);
+      if (accept || L.tries >= kMaxTries) {
+        rotate(L.dir, c, uni(L.k));
+        ++L.k;
+        L.e = L.e / x;
+        ++L.nint;
+        count(true, kStatCompton);
+        if (L.e < S.e_lo) finish(kEnergyWindow, -1, 0);
+        else L.state = kStep;
+      }
+    }
+
+    // ---- one Rayleigh try (material id in the upper half of tries) ----
+    if (L.state == kRayleigh && avail(3)) {
+      const float u1 = uni(L.k), u2 = uni(L.k + 1);
+      L.k += 2;
+      ++L.tries;
+      const float er = L.e / kRestKeV;
+      const float b = s_kappa[L.tries >> 16] * er * er;
+      const float sv = u1 / (1.0f + b * (1.0f - u1));
+      const float c = 1.0f - 2.0f * sv;
+      count(true, kStatTries);
+      if (u2 < 0.5f * (1.0f + c * c) || (L.tries & 0xffff) >= kMaxTries) {
+        rotate(L.dir, c, uni(L.k));
+        ++L.k;
+        ++L.nint;
+        count(true, kStatRayleigh);
+        L.state = kStep;
+      }
+    }
+
+    // ---- the photon reaches the detector cylinder ----
+    if (L.state == kEscape) {
+      const float3 p = L.pos, d = L.dir;
+      const float a = d.x * d.x + d.y * d.y;
+      int cls = kDetected, cr = 0, rg = 0;
+      float nx = 0.0f, ny = 0.0f;
+      if (!(a > 0.0f)) {
+        cls = kLostAxial;
+      } else {
+        const float b = p.x * d.x + p.y * d.y;
+        const float c = p.x * p.x + p.y * p.y - S.r2;
+        const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
+        const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
+        const float hx = p.x + t * d.x, hy = p.y + t * d.y, hz = p.z + t * d.z;
+        L.path += t;
+        if (!(hz >= -S.half_len && hz < S.half_len)) {
+          cls = kLostAxial;
+        } else {
+          rg = max(0, min((int)floorf((hz + S.half_len) * S.inv_pitch), S.n_rings - 1));
+          float phi = atan2f(hy, hx);
+          if (phi < 0.0f) phi += 6.283185307179586f;
+          cr = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
+          nx = hx / S.radius;
+          ny = hy / S.radius;
+          if (L.e < S.e_lo || L.e > S.e_hi) cls = kEnergyWindow;
+        }
+      }
+      count(cls == kDetected, kStatDetected);
+      if (cls != kDetected) {
+        finish(cls, -1, 0);
+      } else if (L.photon == 0) {
+        L.a_cr = cr;
+        L.a_rg = rg;
+        L.a_scat = L.nint;
+        L.a_e = L.e;
+        L.a_path = L.path;
+        L.a_nx = nx;
+        L.a_ny = ny;
+        L.a_dir = L.dir;
+        L.pos = L.e0;  // photon B leaves back to back
+        L.dir = make_float3(-L.d0.x, -L.d0.y, -L.d0.z);
+        L.e = kEmitKeV;
+        L.path = 0.0f;
+        L.nint = 0;
+        L.nsteps = 0;
+        L.photon = 1;
+        L.stream = 2;
+        L.k = 0;
+        L.nb = 0;
+        L.state = kStep;
+      } else if (cr == L.a_cr) {
+        finish(kSameCrystal, -1, 0);
+      } else {
+        L.b_cr = cr;
+        L.b_rg = rg;
+        L.b_nx = nx;
+        L.b_ny = ny;
+        L.state = kCoinc;
+        if (blur) {  // the TOF blur reads stream 0, block 2
+          L.stream = 0;
+          L.k = 8;
+          L.nb = 2;
+        }
+      }
+    }
+
+    // ---- coincidence: TOF, LOR bin, LUT weight, accumulate ----
+    if (L.state == kCoinc && (!blur || avail(2))) {
+      const bool a_first = L.a_cr < L.b_cr;
+      float delta = 0.5f * (a_first ? L.a_path - L.path : L.path - L.a_path);
+      if (blur) {
+        const float g = sqrtf(-2.0f * logf(uni(8))) * cospif(2.0f * uni(9));
+        delta += S.tof_sigma * g;
+      }
+      const long long key_ = a_first ? bin_key(S, L.a_cr, L.b_cr, L.a_rg, L.b_rg, delta)
+                                     : bin_key(S, L.b_cr, L.a_cr, L.b_rg, L.a_rg, delta);
+      const bool scattered = (L.a_scat + L.nint) > 0;
+      const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
+      const bool take = cls == kScatter ? (P.bin_mask & 1) : cls == kTrue ? (P.bin_mask & 2) : false;
+      long long q = 0;
+      if (key_ >= 0 && (take || P.q_out)) {
+        float aa, ab, ba, bb;
+        angles(L.a_nx, L.a_ny, L.a_dir, aa, ab);
+        angles(L.b_nx, L.b_ny, L.dir, ba, bb);
+        const float w = lut_prob<DT>(P.lut, L.a_e, aa, ab, L.a_cr % S.module_t, L.a_rg % S.module_a) *
+                        lut_prob<DT>(P.lut, L.e, ba, bb, L.b_cr % S.module_t, L.b_rg % S.module_a);
+        q = __float2ll_rn(w * 4294967296.0f);
+      }
+      // lanes that hit the same bin add their weights first, one atomic per bin
+      const unsigned act = __activemask();
+      const unsigned takers = __ballot_sync(act, take);
+      if (take) {
+        const unsigned peers = __match_any_sync(takers, (unsigned long long)key_);
+        const unsigned hi = __reduce_add_sync(peers, (unsigned)(q >> 16));
+        const unsigned lo = __reduce_add_sync(peers, (unsigned)(q & 0xffff));
+        if (lane_id == (unsigned)(__ffs(peers) - 1)) {
+          atomicAdd(P.acc + key_, ((unsigned long long)hi << 16) + lo);
+          if (stats) atomicAdd(&s_cnt[kStatAtomics], 1ull);
+        }
+        if (stats) {
+          atomicAdd(&s_cnt[kStatBinned], 1ull);
+          atomicAdd(&s_cnt[kStatWeight], (unsigned long long)q);
+        }
+      }
+      finish(cls, key_, cls == kOutOfRange ? 0 : q);
+    }
+    __syncwarp();
   }
 
-  if (P.stats == nullptr) return;
-  // warp-reduce the counters, one atomic per warp and counter
-  unsigned long long vals[kStatCount] = {};
-#pragma unroll
-  for (int k = 0; k < 8; ++k) vals[k] = cnt.cls[k];
-  vals[kStatSteps] = cnt.steps;
-  vals[kStatCompton] = cnt.compton;
-  vals[kStatRayleigh] = cnt.rayleigh;
-  vals[kStatPhoto] = cnt.photo;
-  vals[kStatBinned] = cnt.binned;
-  vals[kStatWeight] = cnt.weight;
-  vals[kStatRng] = cnt.rng;
-  vals[kStatTries] = cnt.tries;
-  vals[kStatDetected] = cnt.detected;
-#pragma unroll
-  for (int k = 0; k < kStatCount; ++k) {
-    unsigned long long x = vals[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(P.stats + k, x);
-  }
+  if (!stats) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kStatCount; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(P.stats + i, s_cnt[i]);
 }
 
-size_t transport_smem_bytes(const SimParams& p) {
-  return sizeof(float4) * (size_t)p.ph.n_mat * p.ph.n_tab + sizeof(float) * (p.ph.n_tab + kMaxMaterials);
+size_t transport_smem_bytes(const SimParams& p, int block) {
+  return sizeof(float4) * (size_t)p.ph.n_mat * p.ph.n_tab +
+         sizeof(float) * (p.ph.n_tab + kMaxMaterials) + sizeof(uint32_t) * kRingWords * block;
 }
 
 template <int DT>
 static cudaError_t launch_dt(const SimParams& p, int grid, int block, cudaStream_t s) {
-  const size_t smem = transport_smem_bytes(p);
+  const size_t smem = transport_smem_bytes(p, block);
   cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -248,3 +248,19 @@ def test_signa_large_launch_properties(signa):
     r = oracle.simulate(signa.sc, signa.mats, signa.ph, signa.lut, SEED, n - 20_000, 20_000, threads=8)
     compare_histories(tail, r)
     torch.cuda.synchronize()
+
+
+def test_alias_table_equals_oracle(tiny):
+    """The runtime's alias table (thresholds on the Philox word) makes the
+    same accept decision as the oracle's FP64 Vose table for every voxel."""
+    rng = np.random.default_rng(3)
+    act = (tiny.ph.activity * rng.exponential(size=tiny.ph.activity.shape)).astype(np.float32)
+    psc.psc_update_activity(tiny.ctx, tiny.p_id, act)
+    thr, alias = psc.psc_phantom_alias(tiny.ctx, tiny.p_id, act.size)
+    prob, oalias = oracle.alias_build(act)
+    np.testing.assert_array_equal(alias, oalias)
+    # k < thr  <=>  (2k + 1) 2^-24 < prob, checked at the boundary and at random k
+    for k in (thr.astype(np.int64) - 1, thr.astype(np.int64), rng.integers(0, 1 << 23, act.size)):
+        k = np.clip(k, 0, (1 << 23) - 1)
+        np.testing.assert_array_equal(k < thr, (2 * k + 1) * 2.0**-24 < prob)
+    psc.psc_update_activity(tiny.ctx, tiny.p_id, tiny.ph.activity)
