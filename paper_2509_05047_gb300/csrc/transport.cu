@@ -27,7 +27,10 @@
 
 namespace psc {
 
-enum : int { kEmit = 0, kStep = 1, kCompton = 2, kRayleigh = 3, kEscape = 4, kCoinc = 5, kDone = 6 };
+enum : int {
+  kEmit = 0, kStep = 1, kCompton = 2, kRayleigh = 3, kEscape = 4, kCoinc = 5, kNumSections = 6,
+  kFinish = 6, kDone = 7
+};
 
 __device__ __forceinline__ float interp_scalar(const float* t, int n_tab, int e0, float e) {
   const float fe = e - (float)e0;
@@ -136,32 +139,62 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
   L.k = 0;
   L.nb = 0;
 
-  // a history ends: record its class and move to the lane's next history
+  // a history ends: remember its class; the FINISH block records it
+  int fin_cls = 0;
+  long long fin_key = -1, fin_q = 0;
   auto finish = [&](int cls, long long key_out, long long q_out) {
-    const unsigned long long i = L.h - P.first;
-    if (P.cls_out) P.cls_out[i] = (int8_t)cls;
-    if (P.key_out) P.key_out[i] = key_out;
-    if (P.q_out) P.q_out[i] = q_out;
-    if (stats) atomicAdd(&s_cnt[kStatClass0 + cls], 1ull);
-    ++L.m;
-    const unsigned long long idx = gtid + L.m * nthreads;
-    if (idx < P.n) {
-      L.h = P.first + idx;
-      L.state = kEmit;
-      L.stream = 0;
-      L.k = 0;
-      L.nb = 0;
-    } else {
-      L.state = kDone;
-    }
+    fin_cls = cls;
+    fin_key = key_out;
+    fin_q = q_out;
+    L.state = kFinish;
   };
 
+  // per-section cost weights of the warp scheduler (1024 / approximate
+  // instructions of one execution of the section)
+  constexpr int kW[kNumSections] = {1024 / 140, 1024 / 90, 1024 / 70, 1024 / 60, 1024 / 80, 1024 / 300};
+  constexpr int kNeed[kNumSections] = {7, 2, 4, 3, 0, 2};
+
   while (__any_sync(0xffffffffu, L.state != kDone)) {
-    // words the lane's next section reads from the window
-    const int need = L.state == kEmit ? 7 : L.state == kStep ? 2 : L.state == kCompton ? 4
-                   : L.state == kRayleigh ? 3 : (L.state == kCoinc && blur) ? 2 : 0;
-    // ---- refill: the single Philox evaluation of the loop ----
-    if (need && L.k + need > 4 * L.nb) {
+    // ---- FINISH: record the ended history, move to the lane's next one ----
+    if (L.state == kFinish) {
+      const unsigned long long i = L.h - P.first;
+      if (P.cls_out) P.cls_out[i] = (int8_t)fin_cls;
+      if (P.key_out) P.key_out[i] = fin_key;
+      if (P.q_out) P.q_out[i] = fin_q;
+      if (stats) atomicAdd(&s_cnt[kStatClass0 + fin_cls], 1ull);
+      ++L.m;
+      const unsigned long long idx = gtid + L.m * nthreads;
+      if (idx < P.n) {
+        L.h = P.first + idx;
+        L.state = kEmit;
+        L.stream = 0;
+        L.k = 0;
+        L.nb = 0;
+      } else {
+        L.state = kDone;
+      }
+    }
+
+    // ---- warp vote: run the section that serves the most lanes per cost ----
+    int sec = -1, best = 0;
+#pragma unroll
+    for (int q = 0; q < kNumSections; ++q) {
+      const unsigned m = __ballot_sync(0xffffffffu, L.state == q);
+      const int score = __popc(m) * kW[q];
+      if (score > best) {
+        best = score;
+        sec = q;
+      }
+    }
+    if (sec < 0) continue;  // only finished lanes this iteration
+    const bool mine = L.state == sec;
+
+    // ---- refill the section's lanes: the single Philox evaluation ----
+    int need = kNeed[0];
+#pragma unroll
+    for (int q = 1; q < kNumSections; ++q) need = sec == q ? kNeed[q] : need;
+    if (sec == kCoinc && !blur) need = 0;
+    while (mine && L.k + need > 4 * L.nb) {
       const uint4 b = philox4x32_10(make_uint4((uint32_t)L.h, (uint32_t)(L.h >> 32), L.nb, L.stream), key);
       const uint32_t w0 = 4 * L.nb;
       ring[((w0 + 0) & (kRingWords - 1)) * bdim + tid] = b.x;
@@ -171,12 +204,10 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
       ++L.nb;
       count(true, kStatRng);
     }
-    // a section runs only when the words it reads are in the window (a lane
-    // can pass through several sections in one iteration)
-    auto avail = [&](uint32_t n) { return L.k + n <= 4 * L.nb; };
+    if (!mine) continue;
 
     // ---- emission (stream 0, words 0..6) ----
-    if (L.state == kEmit && avail(7)) {
+    if (sec == kEmit) {
       const uint32_t w0 = word(0), w1 = word(1);
       const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
       const uint2 at = __ldg(ph.alias + col);
@@ -203,7 +234,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
 
     // ---- one Woodcock step ----
-    if (L.state == kStep && avail(2)) {
+    if (sec == kStep) {
       bool moved = false;
       if (L.nsteps >= kMaxSteps) {
         finish(kStepLimit, -1, 0);
@@ -253,7 +284,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
 
     // ---- one Klein-Nishina try (Kahn's method on x = E/E') ----
-    if (L.state == kCompton && avail(4)) {
+    if (sec == kCompton) {
       const float r1 = uni(L.k), r2 = uni(L.k + 1), r3 = uni(L.k + 2);
       L.k += 3;
       ++L.tries;
@@ -283,7 +314,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
 
     // ---- one Rayleigh try (material id in the upper half of tries) ----
-    if (L.state == kRayleigh && avail(3)) {
+    if (sec == kRayleigh) {
       const float u1 = uni(L.k), u2 = uni(L.k + 1);
       L.k += 2;
       ++L.tries;
@@ -302,7 +333,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
 
     // ---- the photon reaches the detector cylinder ----
-    if (L.state == kEscape) {
+    if (sec == kEscape) {
       const float3 p = L.pos, d = L.dir;
       const float a = d.x * d.x + d.y * d.y;
       int cls = kDetected, cr = 0, rg = 0;
@@ -368,7 +399,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
 
     // ---- coincidence: TOF, LOR bin, LUT weight, accumulate ----
-    if (L.state == kCoinc && (!blur || avail(2))) {
+    if (sec == kCoinc) {
       const bool a_first = L.a_cr < L.b_cr;
       float delta = 0.5f * (a_first ? L.a_path - L.path : L.path - L.a_path);
       if (blur) {
@@ -407,7 +438,6 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
       }
       finish(cls, key_, cls == kOutOfRange ? 0 : q);
     }
-    __syncwarp();
   }
 
   if (!stats) return;
