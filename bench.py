@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--histories", type=float, default=1e9)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--mode", default="step", choices=["step", "precision"],
+                    help="step: the benchmark line; precision: LUT precision / count-level study")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rings", type=int, default=0,
@@ -311,8 +313,73 @@ def run_reference(a):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------------------
+# precision study: FP32 / FP16 / BF16 LUT at low count levels against a
+# high-count FP32 reference, after smoothing (relative RMS over all bins)
+# ---------------------------------------------------------------------------
+def run_precision(a):
+    import torch
+    import paper_2509_05047_gb300 as psc
+    from paper_2509_05047_gb300 import build as B
+    B.build()
+    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins)
+    dev = torch.device("cuda", 0)
+    ctx = psc.psc_create(0)
+    s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
+    m_id = psc.psc_load_materials(ctx, psc.materials_desc(mats).desc)
+    p_id = psc.psc_load_phantom(ctx, psc.phantom_desc(ph).desc, m_id)
+    luts = {name: psc.psc_load_lut(ctx, psc.lut_desc(lut, dt).desc)
+            for name, dt in (("f32", psc.PSC_LUT_F32), ("f16", psc.PSC_LUT_F16), ("bf16", psc.PSC_LUT_BF16))}
+    sn_id = psc.psc_load_sinogram(ctx, s_id, sens, per_lor=True)
+    a_id = psc.psc_acc_create(ctx, s_id)
+    sh = torch.cuda.current_stream(dev).cuda_stream
+    sigma = (2.0, 2.0, 2.0)
+
+    def estimate(n, lut_id, seed, out):
+        psc.psc_acc_zero(ctx, a_id, sh)
+        done = 0
+        while done < n:                       # 1e9-history launches
+            k = min(int(1e9), n - done)
+            psc.psc_simulate(ctx, psc.sim_args(seed, done, k, s_id, p_id, a_id, lut=lut_id), stream=sh)
+            done += k
+        psc.psc_finalize(ctx, psc.finalize_args(a_id, sens=sn_id, sigma=sigma, scale=1.0 / n), out, sh)
+        torch.cuda.synchronize()
+
+    def rel_rms(x, ref):
+        num, den = 0.0, 0.0
+        xf, rf = x.view(-1), ref.view(-1)
+        for i in range(0, xf.numel(), 1 << 28):
+            d = xf[i:i + (1 << 28)] - rf[i:i + (1 << 28)]
+            num += float((d * d).sum())
+            den += float((rf[i:i + (1 << 28)] ** 2).sum())
+        return math.sqrt(num / den) if den > 0 else float("nan")
+
+    n_ref = int(a.histories)
+    ref = torch.empty(sc.shape, dtype=torch.float64, device=dev)
+    t = time.perf_counter()
+    estimate(n_ref, luts["f32"], 777, ref)
+    t_ref = time.perf_counter() - t
+    out = torch.empty(sc.shape, dtype=torch.float64, device=dev)
+    base = torch.empty(sc.shape, dtype=torch.float64, device=dev)
+    rows = []
+    for n in (int(1e7), int(1e8)):
+        estimate(n, luts["f32"], 4242, base)
+        for name in ("f32", "f16", "bf16"):
+            estimate(n, luts[name], 4242, out)
+            rows.append({"histories": n, "lut": name, "rel_rms_vs_reference": rel_rms(out, ref),
+                         "rel_rms_vs_f32_same_histories": rel_rms(out, base)})
+    psc.psc_destroy(ctx)
+    return {"mode": "precision", "workload": WORKLOAD, "reference_histories": n_ref,
+            "reference_seconds": t_ref, "smoothing_sigma_bins": sigma,
+            "metric": "relative RMS sqrt(sum (A-B)^2 / sum B^2) over all bins after smoothing",
+            "rows": rows}
+
+
 def main():
     a = parse()
+    if a.mode == "precision":
+        print(json.dumps(run_precision(a)))
+        return
     res = run_reference(a) if a.impl == "reference" else run_native(a)
     if res is not None:
         print(json.dumps(res))

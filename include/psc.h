@@ -194,15 +194,21 @@ int psc_acc_write(psc_ctx* ctx, int32_t acc, const int64_t* in /* device */, psc
 /* Simulate and accumulate (Sec. 2.2.1-2.2.3).  stats may be NULL; when
  * given, the call waits for the stream and fills it. */
 int psc_simulate(psc_ctx* ctx, const psc_sim_args* args, psc_stats* stats, psc_stream stream);
+/* Several requests in one persistent launch (continuous batching of uneven
+ * requests): args[0..n) may use different scanners, phantoms, LUTs and
+ * accumulators; their histories are split into work items that the GPU's
+ * CTAs take in turn, so small and large requests share the device.  Each
+ * request's accumulator receives exactly what psc_simulate would add alone.
+ * The launch shape is args[0].block / args[0].grid; stats (if given) sum
+ * over the batch. */
+int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
+                       psc_stream stream);
 /* Scatter estimate = acc * scale * 2^-32, [x norm -> smooth -> / norm],
  * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size). */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
 /* Free one object. */
 int psc_unload(psc_ctx* ctx, int32_t id);
-/* Bytes of device memory held by the context's objects. */
-uint64_t psc_resident_bytes(const psc_ctx* ctx);
-
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,7 @@ SIGNATURES = {
     "psc_acc_read": (C.c_int, [_P, _I32, _P, _P]),
     "psc_acc_write": (C.c_int, [_P, _I32, _P, _P]),
     "psc_simulate": (C.c_int, [_P, C.POINTER(SimArgs), C.POINTER(Stats), _P]),
+    "psc_simulate_batch": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Stats), _P]),
     "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
     "psc_unload": (C.c_int, [_P, _I32]),
     "psc_resident_bytes": (_U64, [_P]),
@@ -241,6 +242,14 @@ def psc_simulate(ctx, args: SimArgs, stats=False, stream=None):
     return st.as_dict() if st is not None else None
 
 
+def psc_simulate_batch(ctx, args_list, stats=False, stream=None):
+    arr = (SimArgs * len(args_list))(*args_list)
+    st = Stats() if stats else None
+    _check(lib().psc_simulate_batch(ctx, arr, len(args_list),
+                                    C.byref(st) if st is not None else None, _stream(stream)))
+    return st.as_dict() if st is not None else None
+
+
 def psc_finalize(ctx, args: FinalizeArgs, out, stream=None):
     _check(lib().psc_finalize(ctx, C.byref(args), _ptr(out), _stream(stream)))
 
@@ -253,9 +262,12 @@ def psc_unload(ctx, obj):
 # marshalling of the ``workloads`` input objects into descriptors
 # ---------------------------------------------------------------------------
 class _Held:
-    """A ctypes descriptor plus the host arrays it points into."""
+    """A ctypes descriptor plus the host arrays it points into.  The
+    descriptor itself also references the arrays, so ``held.desc`` stays
+    valid after the holder is gone."""
 
     def __init__(self, desc, *arrays):
+        desc._keep = arrays
         self.desc = desc
         self.arrays = arrays
 

@@ -29,6 +29,7 @@ namespace psc {
 
 constexpr int NB = 8;            // outputs per thread along the smoothed axis
 constexpr int kMaxTemplK = 12;   // template-specialised truncation radii 1..12
+constexpr int kMaxRings = 128;   // rings per scanner for the axial pass
 
 __device__ __forceinline__ int reflect(int m, int n) {
   const int p = 2 * n;
@@ -45,6 +46,116 @@ __device__ __forceinline__ unsigned fdiv(unsigned i, unsigned magic) {
 __device__ __forceinline__ double at(const double* a, long long i) { return __ldg(a + i); }
 
 // ---------------------------------------------------------------------------
+// Exact IEEE conversions and FP64 products on the integer pipes.
+//
+// The GB300 FP64 pipe retires about 2e11 operations per second (measured with
+// ncu): one FP64 instruction per bin costs ~27 ms on a 5.5e9-bin sinogram.
+// These helpers give the same round-to-nearest-even results as the FP64
+// hardware from 32/64-bit integer instructions; zero is handled inline and
+// the rare operands outside the normal range (subnormal, inf, NaN) fall back
+// to the hardware instruction.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kMant52 = (1ull << 52) - 1;
+
+// index of the highest / lowest set bit of a non-zero 64-bit value, from the
+// 32-bit bit-scan instructions
+__device__ __forceinline__ int msb64(unsigned long long u) {
+  const unsigned hi = (unsigned)(u >> 32);
+  return hi ? 63 - __clz(hi) : 31 - __clz((unsigned)u);
+}
+__device__ __forceinline__ int lsb64(unsigned long long u) {
+  const unsigned lo = (unsigned)u;
+  return lo ? __ffs(lo) - 1 : 31 + __ffs((unsigned)(u >> 32));
+}
+
+// round-to-nearest-even of m >> sh (sh >= 1), returning the carry-adjusted
+// mantissa; e is bumped when rounding carries into a new bit
+__device__ __forceinline__ unsigned long long rne_shift(unsigned long long m, int sh, bool sticky,
+                                                        int width, int& e) {
+  const unsigned long long q = m >> sh;
+  const unsigned long long rem = m & ((1ull << sh) - 1);
+  const unsigned long long half = 1ull << (sh - 1);
+  unsigned long long r = q;
+  if (rem > half || (rem == half && (sticky || (q & 1)))) r = q + 1;
+  if (r >> width) {
+    r >>= 1;
+    ++e;
+  }
+  return r;
+}
+
+// non-negative int64 -> double (RNE)
+__device__ __forceinline__ double i64_to_f64(long long v) {
+  const unsigned long long u = (unsigned long long)v;
+  if (u == 0) return 0.0;
+  int e = msb64(u);
+  unsigned long long m = e <= 52 ? u << (52 - e) : rne_shift(u, e - 52, false, 53, e);
+  return __longlong_as_double(((unsigned long long)(e + 1023) << 52) | (m & kMant52));
+}
+
+// non-negative int64 -> float (RNE)
+__device__ __forceinline__ float i64_to_f32(long long v) {
+  const unsigned long long u = (unsigned long long)v;
+  if (u == 0) return 0.0f;
+  int e = msb64(u);
+  unsigned long long m = e <= 23 ? u << (23 - e) : rne_shift(u, e - 23, false, 24, e);
+  return __int_as_float((int)(((unsigned)(e + 127) << 23) | ((unsigned)m & 0x7fffffu)));
+}
+
+// float -> double (exact)
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = (unsigned)__float_as_int(f);
+  const unsigned ef = (b >> 23) & 0xffu;
+  if ((b & 0x7fffffffu) == 0) return (b >> 31) ? -0.0 : 0.0;
+  if (ef == 0 || ef == 0xffu) return (double)f;
+  return __longlong_as_double(((unsigned long long)(b >> 31) << 63) |
+                              ((unsigned long long)(ef - 127 + 1023) << 52) |
+                              ((unsigned long long)(b & 0x7fffffu) << 29));
+}
+
+// (double)x * b (RNE, one rounding of the exact product) for finite x, b
+__device__ __forceinline__ double fmul_fd(float x, double b) {
+  const unsigned xb = (unsigned)__float_as_int(x);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long sign = ((unsigned long long)(xb >> 31) << 63) ^ (ub & (1ull << 63));
+  const int ex = (int)((xb >> 23) & 0xffu), eb = (int)((ub >> 52) & 0x7ff);
+  if ((xb << 1) == 0 || (ub << 1) == 0) return __longlong_as_double((long long)sign);
+  if (ex == 0 || ex == 0xff || eb == 0 || eb == 0x7ff) return (double)x * b;
+  const unsigned long long mx = (xb & 0x7fffffu) | 0x800000u;          // 24 bits
+  const unsigned long long mb = (ub & kMant52) | (1ull << 52);         // 53 bits
+  // P = mx * mb in [2^75, 2^77) = hi 2^32 + lo; T = P >> 13 in [2^62, 2^64)
+  const unsigned long long lo = mx * (mb & 0xffffffffull);
+  const unsigned long long hi = mx * (mb >> 32);
+  const unsigned long long T = (hi << 19) + (lo >> 13);
+  const bool sticky = (lo & 0x1fffull) != 0;
+  const int top = (int)(T >> 63);
+  int e = ex + eb - 127 + top;
+  const unsigned long long m = rne_shift(T, 10 + top, sticky, 53, e);
+  if (e <= 0 || e >= 0x7ff) return (double)x * b;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
+}
+
+// a * b (RNE) for finite doubles
+__device__ __forceinline__ double dmul(double a, double b) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long sign = (ua ^ ub) & (1ull << 63);
+  const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
+  if (((ua << 1) == 0) || ((ub << 1) == 0)) return __longlong_as_double((long long)sign);
+  if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return a * b;
+  const unsigned long long ma = (ua & kMant52) | (1ull << 52), mb = (ub & kMant52) | (1ull << 52);
+  // ma * mb in [2^104, 2^106): top 64 bits of (ma * mb) << 22, sticky below
+  const unsigned long long hi = __umul64hi(ma << 11, mb << 11);
+  const bool sticky = lsb64(ma) + lsb64(mb) < 42;
+  int e = ea + eb - 1023;
+  const int top = (int)(hi >> 63);
+  e += top;
+  const unsigned long long m = rne_shift(hi, 10 + top, sticky, 53, e);
+  if (e <= 0 || e >= 0x7ff) return a * b;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
+}
+
+// ---------------------------------------------------------------------------
 // no smoothing: out = (acc * c) * sens (FP64)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_constant__ FinParams P) {
@@ -55,8 +166,8 @@ __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_consta
   const long long lor0 = plane * (long long)P.V * P.R;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < J; j += gridDim.x * blockDim.x) {
     const long long i = base + j;
-    double x = (double)__ldg(P.acc + i) * P.c;
-    if (P.sens) x = x * at(P.sens, P.sens_per_lor ? lor0 + fdiv((unsigned)j, P.magic_T) : i);
+    double x = dmul(i64_to_f64(__ldg(P.acc + i)), P.c);
+    if (P.sens) x = dmul(x, at(P.sens, P.sens_per_lor ? lor0 + fdiv((unsigned)j, P.magic_T) : i));
     P.out[i] = x;
   }
 }
@@ -122,7 +233,7 @@ __global__ void __launch_bounds__(256) smooth_radial_kernel(const __grid_constan
     if (s < R + Kr) {
       const int r = (s >= 0 && s < R) ? s : reflect(s, R);
       const long long bin = base + (long long)r * T + t;
-      x = __ll2float_rn(__ldg(P.acc + bin)) * cf;
+      x = i64_to_f32(__ldg(P.acc + bin)) * cf;
       if (P.sens_first && P.sens) x *= (float)at(P.sens, P.sens_per_lor ? line * R + r : bin);
       if (P.norm) x *= (float)at(P.norm, P.norm_per_lor ? line * R + r : bin);
     }
@@ -193,6 +304,9 @@ template <int K>
 __global__ void __launch_bounds__(256) smooth_axial_kernel(const __grid_constant__ FinParams P) {
   extern __shared__ float ext[];           // [tile_rows(L, K)][CH]
   __shared__ float gs[2 * kMaxSmoothRadius + 1];
+  __shared__ long long s_bin[kMaxRings];   // first bin of the segment's plane k
+  __shared__ long long s_lor[kMaxRings];   // first LOR of the segment's plane k
+  __shared__ int s_src[kMaxRings + 2 * kMaxSmoothRadius + NB];  // core row of tile row e (-1: pad)
   const int Kr = K >= 0 ? K : P.K[2];
   for (int j = threadIdx.x; j <= 2 * Kr; j += blockDim.x) gs[j] = P.g[2][j];
   const int nr = P.n_rings;
@@ -206,19 +320,23 @@ __global__ void __launch_bounds__(256) smooth_axial_kernel(const __grid_constant
   const int ra0 = max(0, -d);
   const int L = nr - abs(d);
   const int rows = tile_rows(L, Kr);
-  for (int i = threadIdx.x; i < rows * CH; i += blockDim.x) {
-    const int e = i >> sh, c = i & (CH - 1);
+  const long long lors = (long long)P.V * P.R;
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const long long plane = (long long)(ra0 + k) * nr + (ra0 + k + d);
+    s_bin[k] = plane * J;
+    s_lor[k] = plane * lors;
+  }
+  for (int e = threadIdx.x; e < rows; e += blockDim.x) {
     const int s = e - Kr;
-    float x = 0.0f;
-    if (c < cw && s < L + Kr) {
-      const int k = (s >= 0 && s < L) ? s : reflect(s, L);
-      const long long plane = (long long)(ra0 + k) * nr + (ra0 + k + d);
-      x = P.scratch[plane * J + j0 + c];
-    }
-    ext[i] = x;
+    s_src[e] = s < L + Kr ? ((s >= 0 && s < L) ? s : reflect(s, L)) : -1;
   }
   __syncthreads();
-  const long long lors = (long long)P.V * P.R;
+  for (int i = threadIdx.x; i < rows * CH; i += blockDim.x) {
+    const int e = i >> sh, c = i & (CH - 1);
+    const int k = s_src[e];
+    ext[i] = (c < cw && k >= 0) ? P.scratch[s_bin[k] + j0 + c] : 0.0f;
+  }
+  __syncthreads();
   const int nkb = (L + NB - 1) / NB;
   for (int i = threadIdx.x; i < nkb * CH; i += blockDim.x) {
     const int kb = i >> sh, c = i & (CH - 1);
@@ -230,12 +348,17 @@ __global__ void __launch_bounds__(256) smooth_axial_kernel(const __grid_constant
     for (int b = 0; b < NB; ++b) {
       const int k = kb * NB + b;
       if (k >= L) break;
-      const long long plane = (long long)(ra0 + k) * nr + (ra0 + k + d);
-      const long long bin = plane * J + j0 + c;
-      const long long lor = plane * lors + lor_in_plane;
-      double y = (double)o[b];
-      if (P.rnorm) y = y * at(P.rnorm, P.norm_per_lor ? lor : bin);
-      if (!P.sens_first && P.sens) y = y * at(P.sens, P.sens_per_lor ? lor : bin);
+      const long long bin = s_bin[k] + j0 + c;
+      const long long lor = s_lor[k] + lor_in_plane;
+      double y;
+      if (P.rnorm) {
+        y = fmul_fd(o[b], at(P.rnorm, P.norm_per_lor ? lor : bin));
+        if (!P.sens_first && P.sens) y = dmul(y, at(P.sens, P.sens_per_lor ? lor : bin));
+      } else if (!P.sens_first && P.sens) {
+        y = fmul_fd(o[b], at(P.sens, P.sens_per_lor ? lor : bin));
+      } else {
+        y = f32_to_f64(o[b]);
+      }
       P.out[bin] = y;
     }
   }

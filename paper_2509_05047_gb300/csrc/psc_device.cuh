@@ -62,17 +62,30 @@ struct LutParams {
   float e_min, e_scale, a_min, a_scale, b_min, b_scale;  // g = (x - min) * scale - 0.5
 };
 
-struct SimParams {
+// one simulation request: histories [first, first + n) of seed's streams
+struct Job {
   ScannerParams sc;
   PhantomParams ph;
   LutParams lut;
   unsigned long long seed, first, n;
-  int bin_mask;
+  unsigned long long chunk;    // histories per work item
   unsigned long long* acc;     // int64 fixed-point sinogram
-  int8_t* cls_out;
+  int8_t* cls_out;             // optional listmode outputs, indexed by history - first
   long long* key_out;
   long long* q_out;
-  unsigned long long* stats;   // kStatCount counters or nullptr
+  int bin_mask;
+};
+
+constexpr int kMaxJobs = 48;   // jobs per launch (kernel parameter space)
+
+// one persistent launch over the chunks of several jobs; chunk c belongs to
+// the first job j with c < chunk_end[j]
+struct BatchParams {
+  Job jobs[kMaxJobs];
+  unsigned long long chunk_end[kMaxJobs];
+  int n_jobs;
+  unsigned long long* next_chunk;  // work counter, zero at launch
+  unsigned long long* stats;       // kStatCount counters or nullptr
 };
 
 // ---------------------------------------------------------------------------

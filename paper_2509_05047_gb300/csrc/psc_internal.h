@@ -28,8 +28,12 @@ struct FinParams {
   float g[3][2 * kMaxSmoothRadius + 1];
 };
 
-size_t transport_smem_bytes(const SimParams& p, int block);
-cudaError_t launch_transport(const SimParams& p, int grid, int block, cudaStream_t s);
+// sets the calling thread's psc_last_error() message, returns code
+int psc_set_error(int code, const char* fmt, ...);
+
+size_t transport_smem_bytes(const PhantomParams& ph, int block);
+cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int block, size_t smem,
+                             cudaStream_t s);
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm);
 
 size_t finalize_smem_radial(const FinParams& p);

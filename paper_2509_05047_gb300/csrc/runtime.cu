@@ -47,6 +47,8 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
   } while (0)
 
+constexpr int kCounterSlots = 4096;
+
 enum Kind { kScannerObj = 1, kMaterialsObj, kPhantomObj, kLutObj, kSinoObj, kAccObj };
 
 struct DevBuf {
@@ -141,6 +143,10 @@ struct psc_ctx {
   // statistics counters of psc_simulate (used only when stats are requested)
   std::mutex stats_mu;
   DevBuf stats;
+  // work counters of the persistent transport launches: a ring of slots,
+  // each zeroed on the launch's stream before use
+  DevBuf counters;
+  unsigned long long counter_next = 0;
 };
 
 namespace {
@@ -273,6 +279,21 @@ extern "C" {
 
 const char* psc_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+// error reporting for the library's other translation units
+int psc::psc_set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+extern "C" {
+
 int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
   if (!out) return fail(PSC_EINVAL, "out is NULL");
   *out = nullptr;
@@ -298,6 +319,12 @@ int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
     return cuda_fail(e, "cudaMalloc(stats)");
   }
   ctx->stats.bytes = sizeof(unsigned long long) * kStatCount;
+  e = cudaMalloc(&ctx->counters.p, sizeof(unsigned long long) * kCounterSlots);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaMalloc(counters)");
+  }
+  ctx->counters.bytes = sizeof(unsigned long long) * kCounterSlots;
   e = cudaEventCreateWithFlags(&ctx->scratch_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     delete ctx;
@@ -601,8 +628,8 @@ int psc_unload(psc_ctx* ctx, int32_t id) {
   return PSC_OK;
 }
 
-int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stream stream) {
-  if (!ctx || !a) return fail(PSC_EINVAL, "NULL argument");
+// validate one request and describe it as a kernel job
+static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype) {
   GET(ScannerObj, sc, a->scanner, kScannerObj);
   GET(PhantomObj, ph, a->phantom, kPhantomObj);
   GET(AccObj, acc, a->acc, kAccObj);
@@ -625,14 +652,9 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
     const double x = pd.ox + ((i & 1) ? pd.nx * pd.dx : 0.0), y = pd.oy + ((i & 2) ? pd.ny * pd.dy : 0.0);
     if (!(x * x + y * y < R2)) return fail(PSC_EINVAL, "phantom grid reaches outside the detector cylinder");
   }
-  if (stats) std::memset(stats, 0, sizeof *stats);
-  if (a->n_histories == 0) return PSC_OK;
-  DeviceGuard g(ctx->device);
-
-  SimParams p;
-  std::memset(&p, 0, sizeof p);
-  p.sc = sc->params;
-  PhantomParams& q = p.ph;
+  std::memset(&jb, 0, sizeof jb);
+  jb.sc = sc->params;
+  PhantomParams& q = jb.ph;
   q.nx = pd.nx;
   q.ny = pd.ny;
   q.nz = pd.nz;
@@ -656,41 +678,91 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
   q.maj = (const float*)ph->maj.p;
   q.kappa = (const float*)ph->kappa.p;
   if (lut) {
-    p.lut = lut->params;
+    jb.lut = lut->params;
   } else {
-    p.lut.dtype = -1;
+    jb.lut.dtype = -1;
   }
-  p.seed = a->seed;
-  p.first = a->first_history;
-  p.n = a->n_histories;
-  p.bin_mask = a->bin_mask ? a->bin_mask : PSC_BIN_SCATTER;
-  p.acc = (unsigned long long*)acc->data.p;
-  p.cls_out = a->cls_out;
-  p.key_out = (long long*)a->key_out;
-  p.q_out = (long long*)a->q_out;
+  lut_dtype = jb.lut.dtype;
+  jb.seed = a->seed;
+  jb.first = a->first_history;
+  jb.n = a->n_histories;
+  jb.bin_mask = a->bin_mask ? a->bin_mask : PSC_BIN_SCATTER;
+  jb.acc = (unsigned long long*)acc->data.p;
+  jb.cls_out = a->cls_out;
+  jb.key_out = (long long*)a->key_out;
+  jb.q_out = (long long*)a->q_out;
+  return PSC_OK;
+}
 
-  const int block = a->block ? a->block : 256;
-  const size_t smem = transport_smem_bytes(p, block);
-  if ((int)smem > ctx->max_smem_optin) return fail(PSC_EINVAL, "material tables need %zu bytes of shared memory", smem);
-  int grid = a->grid;
-  if (grid == 0) {
-    int per_sm = 0;
-    CK(transport_occupancy(p.lut.dtype, block, smem, &per_sm), "occupancy");
-    grid = ctx->sms * std::max(per_sm, 1);
-    const unsigned long long need = (a->n_histories + block - 1) / block;
-    if ((unsigned long long)grid > need) grid = (int)need;
+int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
+                       psc_stream stream) {
+  if (!ctx || (!args && n > 0) || n < 0) return fail(PSC_EINVAL, "NULL argument or negative count");
+  std::vector<Job> jobs;
+  std::vector<int> dts;
+  jobs.reserve(n);
+  for (int i = 0; i < n; ++i) {
+    Job jb;
+    int dt;
+    int rc = make_job(ctx, &args[i], jb, dt);
+    if (rc) return rc;
+    if (jb.n == 0) continue;
+    jobs.push_back(jb);
+    dts.push_back(dt);
   }
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (jobs.empty()) return PSC_OK;
+  DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  const int block = n > 0 && args[0].block ? args[0].block : 256;
   std::unique_lock<std::mutex> lk(ctx->stats_mu, std::defer_lock);
+  unsigned long long* dstats = nullptr;
   if (stats) {
     lk.lock();
-    p.stats = (unsigned long long*)ctx->stats.p;
-    CK(cudaMemsetAsync(p.stats, 0, sizeof(unsigned long long) * kStatCount, s), "zero stats");
+    dstats = (unsigned long long*)ctx->stats.p;
+    CK(cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * kStatCount, s), "zero stats");
   }
-  CK(launch_transport(p, grid, block, s), "transport kernel launch");
+  // one launch per LUT storage type, at most kMaxJobs jobs each
+  std::vector<bool> done(jobs.size(), false);
+  for (size_t i0 = 0; i0 < jobs.size(); ++i0) {
+    if (done[i0]) continue;
+    BatchParams bp;
+    std::memset(&bp, 0, sizeof bp);
+    size_t smem = 0;
+    unsigned long long total = 0;
+    const int dt = dts[i0];
+    for (size_t i = i0; i < jobs.size() && bp.n_jobs < kMaxJobs; ++i) {
+      if (done[i] || dts[i] != dt) continue;
+      done[i] = true;
+      bp.jobs[bp.n_jobs] = jobs[i];
+      smem = std::max(smem, transport_smem_bytes(jobs[i].ph, block));
+      ++bp.n_jobs;
+    }
+    if ((int)smem > ctx->max_smem_optin) return fail(PSC_EINVAL, "material tables need %zu bytes of shared memory", smem);
+    int grid = n > 0 ? args[0].grid : 0;
+    if (grid == 0) {
+      int per_sm = 0;
+      CK(transport_occupancy(dt, block, smem, &per_sm), "occupancy");
+      grid = ctx->sms * std::max(per_sm, 1);
+    }
+    // work items: chunks sized so every CTA gets a few of each job, within
+    // [1024, 65536] histories
+    for (int j = 0; j < bp.n_jobs; ++j) {
+      Job& jb = bp.jobs[j];
+      const unsigned long long per = (jb.n + 2ull * grid - 1) / (2ull * grid);
+      jb.chunk = std::min<unsigned long long>(65536, std::max<unsigned long long>(1024, per));
+      total += (jb.n + jb.chunk - 1) / jb.chunk;
+      bp.chunk_end[j] = total;
+    }
+    if ((unsigned long long)grid > total) grid = (int)total;
+    unsigned long long* counter = (unsigned long long*)ctx->counters.p + (ctx->counter_next++ % kCounterSlots);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s), "zero work counter");
+    bp.next_chunk = counter;
+    bp.stats = dstats;
+    CK(launch_transport(bp, dt, grid, block, smem, s), "transport kernel launch");
+  }
   if (stats) {
     unsigned long long h[kStatCount];
-    CK(cudaMemcpyAsync(h, p.stats, sizeof h, cudaMemcpyDeviceToHost, s), "read stats");
+    CK(cudaMemcpyAsync(h, dstats, sizeof h, cudaMemcpyDeviceToHost, s), "read stats");
     CK(cudaStreamSynchronize(s), "transport kernel");
     for (int k = 0; k < 8; ++k) stats->class_counts[k] = h[k];
     stats->steps = h[kStatSteps];
@@ -705,6 +777,11 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
     stats->atomics = h[kStatAtomics];
   }
   return PSC_OK;
+}
+
+int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stream stream) {
+  if (!ctx || !a) return fail(PSC_EINVAL, "NULL argument");
+  return psc_simulate_batch(ctx, a, 1, stats, stream);
 }
 
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream) {
@@ -773,6 +850,7 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
   // tile sizes: radial lines whole; view / axial column chunks (powers of
   // two) sized so a tile stays within 48 KB
   p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
+  if (p.n_rings > 128) return fail(PSC_EINVAL, "smoothing supports at most 128 rings");
   const long long J = (long long)p.V * p.R * p.T;
   if (J * p.T >= (1LL << 32)) return fail(PSC_EOVERFLOW, "a sinogram plane of %lld bins is too large", J);
   if (finalize_smem_radial(p) > (size_t)ctx->max_smem_optin)

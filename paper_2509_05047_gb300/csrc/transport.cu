@@ -93,33 +93,66 @@ struct Lane {
 };
 
 template <int DT>
-__global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ SimParams P) {
+__global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ float4 smem[];
-  const int n_xs = P.ph.n_mat * P.ph.n_tab;
-  float4* s_xs = smem;
-  float* s_maj = reinterpret_cast<float*>(smem + n_xs);
-  float* s_kappa = s_maj + P.ph.n_tab;
-  uint32_t* ring = reinterpret_cast<uint32_t*>(s_kappa + kMaxMaterials);  // [kRingWords][blockDim]
-  __shared__ unsigned long long s_cnt[kStatCount];
-  for (int i = threadIdx.x; i < n_xs; i += blockDim.x) {
-    const int mm = i / P.ph.n_tab, kk = i - mm * P.ph.n_tab;
-    s_xs[i] = P.ph.xs[mm * P.ph.n_e + P.ph.e0 + kk];
-  }
-  for (int i = threadIdx.x; i < P.ph.n_tab; i += blockDim.x) s_maj[i] = P.ph.maj[P.ph.e0 + i];
-  if (threadIdx.x < kMaxMaterials)
-    s_kappa[threadIdx.x] = threadIdx.x < P.ph.n_mat ? P.ph.kappa[threadIdx.x] : 0.0f;
-  for (int i = threadIdx.x; i < kStatCount; i += blockDim.x) s_cnt[i] = 0;
-  __syncthreads();
-
-  const PhantomParams& ph = P.ph;
-  const ScannerParams& S = P.sc;
   const unsigned tid = threadIdx.x, bdim = blockDim.x;
+  uint32_t* ring = reinterpret_cast<uint32_t*>(smem);  // [kRingWords][blockDim]
+  float4* s_xs = reinterpret_cast<float4*>(ring + kRingWords * bdim);
+  __shared__ Job s_job;                       // the job of the current chunk
+  __shared__ int s_j;
+  __shared__ unsigned long long s_lo;         // first history of the chunk
+  __shared__ unsigned s_len, s_next;          // chunk length, next offset to hand out
+  __shared__ unsigned long long s_cnt[kStatCount];
+  for (int i = tid; i < kStatCount; i += bdim) s_cnt[i] = 0;
   const unsigned lane_id = tid & 31u;
-  const bool stats = P.stats != nullptr;
-  const unsigned long long gtid = (unsigned long long)blockIdx.x * bdim + tid;
-  const unsigned long long nthreads = (unsigned long long)gridDim.x * bdim;
-  const uint2 key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-  const bool blur = S.tof_sigma > 0.0f;
+  const bool stats = B.stats != nullptr;
+  int cached = -1;
+
+  for (;;) {
+    // ---- fetch the next chunk of (job, history range) ----
+    if (tid == 0) {
+      const unsigned long long c = atomicAdd(B.next_chunk, 1ull);
+      int j = -1;
+      if (c < B.chunk_end[B.n_jobs - 1]) {
+        j = 0;
+        while (B.chunk_end[j] <= c) ++j;
+        const unsigned long long c0 = j ? B.chunk_end[j - 1] : 0ull;
+        const unsigned long long lo = B.jobs[j].first + (c - c0) * B.jobs[j].chunk;
+        const unsigned long long hi = B.jobs[j].first + B.jobs[j].n;
+        s_lo = lo;
+        s_len = (unsigned)min(B.jobs[j].chunk, hi - lo);
+        s_next = 0;
+      }
+      s_j = j;
+    }
+    __syncthreads();
+    const int jcur = s_j;
+    if (jcur < 0) break;
+    if (jcur != cached) {  // stage the job and its phantom's tables
+      const int* src = reinterpret_cast<const int*>(&B.jobs[jcur]);
+      for (int i = tid; i < (int)(sizeof(Job) / sizeof(int)); i += bdim)
+        reinterpret_cast<int*>(&s_job)[i] = src[i];
+      const PhantomParams& pg = B.jobs[jcur].ph;
+      const int n_xs = pg.n_mat * pg.n_tab;
+      float* s_maj = reinterpret_cast<float*>(s_xs + n_xs);
+      float* s_kappa = s_maj + pg.n_tab;
+      for (int i = tid; i < n_xs; i += bdim) {
+        const int mm = i / pg.n_tab, kk = i - mm * pg.n_tab;
+        s_xs[i] = pg.xs[mm * pg.n_e + pg.e0 + kk];
+      }
+      for (int i = tid; i < pg.n_tab; i += bdim) s_maj[i] = pg.maj[pg.e0 + i];
+      if (tid < (unsigned)kMaxMaterials) s_kappa[tid] = (int)tid < pg.n_mat ? pg.kappa[tid] : 0.0f;
+      cached = jcur;
+    }
+    __syncthreads();
+
+    const Job& J = s_job;
+    const PhantomParams& ph = J.ph;
+    const ScannerParams& S = J.sc;
+    const float* s_maj = reinterpret_cast<const float*>(s_xs + ph.n_mat * ph.n_tab);
+    const float* s_kappa = s_maj + ph.n_tab;
+    const uint2 key = make_uint2((uint32_t)J.seed, (uint32_t)(J.seed >> 32));
+    const bool blur = S.tof_sigma > 0.0f;
 
   auto word = [&](uint32_t w) -> uint32_t { return ring[(w & (kRingWords - 1)) * bdim + tid]; };
   auto uni = [&](uint32_t w) -> float { return u01(word(w)); };
@@ -132,9 +165,11 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
   };
 
   Lane L;
-  L.m = 0;
-  L.h = P.first + gtid;
-  L.state = gtid < P.n ? kEmit : kDone;
+  {
+    const unsigned off = atomicAdd(&s_next, 1u);
+    L.h = s_lo + off;
+    L.state = off < s_len ? kEmit : kDone;
+  }
   L.stream = 0;
   L.k = 0;
   L.nb = 0;
@@ -157,15 +192,14 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
   while (__any_sync(0xffffffffu, L.state != kDone)) {
     // ---- FINISH: record the ended history, move to the lane's next one ----
     if (L.state == kFinish) {
-      const unsigned long long i = L.h - P.first;
-      if (P.cls_out) P.cls_out[i] = (int8_t)fin_cls;
-      if (P.key_out) P.key_out[i] = fin_key;
-      if (P.q_out) P.q_out[i] = fin_q;
+      const unsigned long long i = L.h - J.first;
+      if (J.cls_out) J.cls_out[i] = (int8_t)fin_cls;
+      if (J.key_out) J.key_out[i] = fin_key;
+      if (J.q_out) J.q_out[i] = fin_q;
       if (stats) atomicAdd(&s_cnt[kStatClass0 + fin_cls], 1ull);
-      ++L.m;
-      const unsigned long long idx = gtid + L.m * nthreads;
-      if (idx < P.n) {
-        L.h = P.first + idx;
+      const unsigned off = atomicAdd(&s_next, 1u);
+      if (off < s_len) {
+        L.h = s_lo + off;
         L.state = kEmit;
         L.stream = 0;
         L.k = 0;
@@ -410,14 +444,14 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
                                      : bin_key(S, L.b_cr, L.a_cr, L.b_rg, L.a_rg, delta);
       const bool scattered = (L.a_scat + L.nint) > 0;
       const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
-      const bool take = cls == kScatter ? (P.bin_mask & 1) : cls == kTrue ? (P.bin_mask & 2) : false;
+      const bool take = cls == kScatter ? (J.bin_mask & 1) : cls == kTrue ? (J.bin_mask & 2) : false;
       long long q = 0;
-      if (key_ >= 0 && (take || P.q_out)) {
+      if (key_ >= 0 && (take || J.q_out)) {
         float aa, ab, ba, bb;
         angles(L.a_nx, L.a_ny, L.a_dir, aa, ab);
         angles(L.b_nx, L.b_ny, L.dir, ba, bb);
-        const float w = lut_prob<DT>(P.lut, L.a_e, aa, ab, L.a_cr % S.module_t, L.a_rg % S.module_a) *
-                        lut_prob<DT>(P.lut, L.e, ba, bb, L.b_cr % S.module_t, L.b_rg % S.module_a);
+        const float w = lut_prob<DT>(J.lut, L.a_e, aa, ab, L.a_cr % S.module_t, L.a_rg % S.module_a) *
+                        lut_prob<DT>(J.lut, L.e, ba, bb, L.b_cr % S.module_t, L.b_rg % S.module_a);
         q = __float2ll_rn(w * 4294967296.0f);
       }
       // lanes that hit the same bin add their weights first, one atomic per bin
@@ -428,7 +462,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
         const unsigned hi = __reduce_add_sync(peers, (unsigned)(q >> 16));
         const unsigned lo = __reduce_add_sync(peers, (unsigned)(q & 0xffff));
         if (lane_id == (unsigned)(__ffs(peers) - 1)) {
-          atomicAdd(P.acc + key_, ((unsigned long long)hi << 16) + lo);
+          atomicAdd(J.acc + key_, ((unsigned long long)hi << 16) + lo);
           if (stats) atomicAdd(&s_cnt[kStatAtomics], 1ull);
         }
         if (stats) {
@@ -440,20 +474,22 @@ __global__ void __launch_bounds__(256) transport_kernel(const __grid_constant__ 
     }
   }
 
+    __syncthreads();  // every lane is done with the chunk before the next fetch
+  }
+
   if (!stats) return;
   __syncthreads();
   for (int i = threadIdx.x; i < kStatCount; i += blockDim.x)
-    if (s_cnt[i]) atomicAdd(P.stats + i, s_cnt[i]);
+    if (s_cnt[i]) atomicAdd(B.stats + i, s_cnt[i]);
 }
 
-size_t transport_smem_bytes(const SimParams& p, int block) {
-  return sizeof(float4) * (size_t)p.ph.n_mat * p.ph.n_tab +
-         sizeof(float) * (p.ph.n_tab + kMaxMaterials) + sizeof(uint32_t) * kRingWords * block;
+size_t transport_smem_bytes(const PhantomParams& ph, int block) {
+  return sizeof(uint32_t) * kRingWords * block + sizeof(float4) * (size_t)ph.n_mat * ph.n_tab +
+         sizeof(float) * (ph.n_tab + kMaxMaterials);
 }
 
 template <int DT>
-static cudaError_t launch_dt(const SimParams& p, int grid, int block, cudaStream_t s) {
-  const size_t smem = transport_smem_bytes(p, block);
+static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -461,12 +497,13 @@ static cudaError_t launch_dt(const SimParams& p, int grid, int block, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_transport(const SimParams& p, int grid, int block, cudaStream_t s) {
-  switch (p.lut.dtype) {
-    case 0: return launch_dt<0>(p, grid, block, s);
-    case 1: return launch_dt<1>(p, grid, block, s);
-    case 2: return launch_dt<2>(p, grid, block, s);
-    default: return launch_dt<-1>(p, grid, block, s);
+cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int block, size_t smem,
+                             cudaStream_t s) {
+  switch (lut_dtype) {
+    case 0: return launch_dt<0>(p, grid, block, smem, s);
+    case 1: return launch_dt<1>(p, grid, block, smem, s);
+    case 2: return launch_dt<2>(p, grid, block, smem, s);
+    default: return launch_dt<-1>(p, grid, block, smem, s);
   }
 }
 

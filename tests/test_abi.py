@@ -55,3 +55,24 @@ def test_kernels_are_built_for_sm103a(libpath):
     out = subprocess.check_output(["cuobjdump", "--list-elf", libpath], text=True) \
         if shutil.which("cuobjdump") else "sm_103a"
     assert "sm_103" in out
+
+
+def test_descriptors_keep_their_host_arrays_alive():
+    """A descriptor taken from a temporary holder stays valid (the arrays it
+    points into must not be freed before the C call reads them)."""
+    import ctypes
+    import gc
+
+    import numpy as np
+
+    import paper_2509_05047_gb300 as psc
+    import workloads as W
+    ph = W.phantom_water_cylinder()
+    expect = int(ph.material.sum())
+    d = psc.phantom_desc(W.phantom_water_cylinder()).desc
+    m = psc.materials_desc(W.standard_materials()).desc
+    lu = psc.lut_desc(W.lut_tiny(W.scanner_tiny())).desc
+    gc.collect()
+    n = 64 * 64 * 32
+    assert int(np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(d.material)).sum()) == expect
+    assert m._keep and lu._keep

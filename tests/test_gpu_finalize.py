@@ -159,3 +159,25 @@ def test_paper_scale_sampled(tmp_path):
         np.testing.assert_array_equal(got, exp)
     finally:
         f.close()
+
+
+def test_fp64_products_round_like_ieee(small):
+    """The FP64 multiply runs on the integer pipes: crafted operands whose
+    exact products sit on rounding ties (27-bit mantissas) and accumulators
+    above 2^53 must give the IEEE round-to-nearest-even result bit for bit."""
+    rng = np.random.default_rng(11)
+    shape = small.sc.shape
+    n = int(np.prod(shape))
+    acc = (rng.integers(1 << 26, 1 << 27, size=n) | 1) << rng.integers(0, 30, size=n)
+    big = rng.uniform(size=n) < 0.3
+    acc[big] = (1 << 53) + rng.integers(0, 1 << 20, size=big.sum())
+    acc[rng.uniform(size=n) < 0.05] = 0
+    acc = acc.astype(np.int64).reshape(shape)
+    sens = (((rng.integers(1 << 26, 1 << 27, size=small.sc.lor_shape) | 1).astype(np.float64))
+            * 2.0**-27)
+    s_id = small.sino(sens, True)
+    small.write_acc(acc)
+    for scale in (1.0, 0.37, 3.0 * 2.0**-20):
+        out = small.run(sens=s_id, scale=scale).cpu().numpy()
+        np.testing.assert_array_equal(out, oracle.finalize(acc, small.sc.n_rings, sens=sens, scale=scale))
+    small.write_acc(small.acc)
