@@ -207,6 +207,27 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
  * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size). */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
+/* Allocation-free variant of psc_finalize for callers that cannot allocate
+ * device memory (their device memory belongs to another allocator, is
+ * capped, or must not be allocated once a real-time loop is running).  The
+ * paper has no counterpart.  Inputs and the output are the caller's device
+ * arrays: acc int64 and out f64 of n_rings^2 x (n_crystals/2) x n_rad x
+ * n_tof bins; sens / norm (NULL = none) per LOR when *_per_lor, else per
+ * bin; sigma (host [3], NULL = no smoothing), scale and sens_first as in
+ * psc_finalize_args.  The smoothing's working memory is one static device
+ * array of 64 MiB per GPU (held from library load until process exit):
+ * sinograms needing more than 4 bytes per bin plus 8 per normalisation
+ * value (256-byte aligned) are rejected with PSC_EOVERFLOW.  No cudaMalloc,
+ * cudaFree or allocating library call is made.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls on a device share the
+ * array and every call overwrites all of it that it reads, so nothing
+ * needs clearing; calls that overlap on the GPU (other streams, other
+ * threads) race on it and must be ordered by the caller. */
+int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t n_crystals, int32_t n_rad,
+                        int32_t n_tof, const double* sens, int32_t sens_per_lor,
+                        const double* norm, int32_t norm_per_lor, const double* sigma,
+                        double scale, int32_t sens_first, double* out, psc_stream stream);
 /* Free one object. */
 int psc_unload(psc_ctx* ctx, int32_t id);
 #ifdef __cplusplus

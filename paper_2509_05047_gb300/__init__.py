@@ -110,6 +110,8 @@ SIGNATURES = {
     "psc_simulate": (C.c_int, [_P, C.POINTER(SimArgs), C.POINTER(Stats), _P]),
     "psc_simulate_batch": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Stats), _P]),
     "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
+    "psc_finalize_static": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _I32, _P,
+                                      C.c_double, _I32, _P, _P]),
     "psc_unload": (C.c_int, [_P, _I32]),
     "psc_resident_bytes": (_U64, [_P]),
 }
@@ -252,6 +254,16 @@ def psc_simulate_batch(ctx, args_list, stats=False, stream=None):
 
 def psc_finalize(ctx, args: FinalizeArgs, out, stream=None):
     _check(lib().psc_finalize(ctx, C.byref(args), _ptr(out), _stream(stream)))
+
+
+def psc_finalize_static(acc, n_rings, n_crystals, n_rad, n_tof, out, sens=None, sens_per_lor=True,
+                        norm=None, norm_per_lor=True, sigma=None, scale=1.0, sens_first=False,
+                        stream=None):
+    """Allocation-free finalize on caller-owned device arrays (see psc.h)."""
+    sig = (C.c_double * 3)(*sigma) if sigma is not None else None
+    _check(lib().psc_finalize_static(_ptr(acc), n_rings, n_crystals, n_rad, n_tof, _ptr(sens),
+                                     1 if sens_per_lor else 0, _ptr(norm), 1 if norm_per_lor else 0,
+                                     sig, scale, 1 if sens_first else 0, _ptr(out), _stream(stream)))
 
 
 def psc_unload(ctx, obj):
