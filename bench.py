@@ -38,8 +38,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--histories", type=float, default=1e9)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "precision"],
-                    help="step: the benchmark line; precision: LUT precision / count-level study")
+    ap.add_argument("--mode", default="step", choices=["step", "precision", "batched", "served"],
+                    help="step: the benchmark line; precision: LUT precision / count-level study; "
+                         "batched / served: request server vs plain sequential requests")
+    ap.add_argument("--requests", type=int, default=32, help="batched: phantoms; served: chains")
+    ap.add_argument("--rate", type=float, default=20.0, help="served: mean request arrivals per s")
+    ap.add_argument("--max-active", type=int, default=4)
+    ap.add_argument("--budget-scale", type=float, default=1.0,
+                    help="multiply the 1e6-1e9 history budgets (shorter runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rings", type=int, default=0,
@@ -174,13 +180,17 @@ def run_native(a):
     fin = psc.finalize_args(a_id, sens=sn_id, sigma=(2.0, 2.0, 2.0), scale=1.0 / n)
 
     def step(i, ev=None):
-        psc.psc_acc_zero(ctx, a_id, sh)
         if ev is not None:
             ev[0].record(stream)
-        psc.psc_simulate(ctx, psc.sim_args(seed, i * n, n, s_id, p_id, a_id, lut=l_id), stream=sh)
+        psc.psc_acc_zero(ctx, a_id, sh)
         if ev is not None:
             ev[1].record(stream)
+        psc.psc_simulate(ctx, psc.sim_args(seed, i * n, n, s_id, p_id, a_id, lut=l_id), stream=sh)
+        if ev is not None:
+            ev[2].record(stream)
         psc.psc_finalize(ctx, fin, out, sh)
+        if ev is not None:
+            ev[3].record(stream)
 
     # counters of one step's transport (for the algorithmic-work roofline)
     psc.psc_acc_zero(ctx, a_id, sh)
@@ -191,8 +201,7 @@ def run_native(a):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(a.steps)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(a.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -204,7 +213,8 @@ def run_native(a):
     if world > 1:
         dist.barrier()
     ms = t0.elapsed_time(t1)
-    kern_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    phase = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(3)] for e in evs]).mean(axis=0)
+    kern_ms = float(phase[1])
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -251,6 +261,8 @@ def run_native(a):
                       "parallelism": f"replicas{world}"},
            "roofline": roofline, "clocks": clocks, "e2e": e2e,
            "gpu_launches": 4 * a.steps,
+           "phases_ms": {"acc_zero": round(float(phase[0]), 3), "transport": round(float(phase[1]), 3),
+                         "finalize": round(float(phase[2]), 3)},
            "transport_stats": {k: int(v) for k, v in st.items()}}
     if rank == 0 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(sc, mats, ph, lut, sens, n, budget_s=20.0)
@@ -375,8 +387,174 @@ def run_precision(a):
             "rows": rows}
 
 
+# ---------------------------------------------------------------------------
+# batched / served requests against plain sequential requests
+# ---------------------------------------------------------------------------
+def _request_mix(a, served):
+    """(kind, phantom builder key, budget, seed) per request.  batched: one
+    request per seeded ellipsoid torso (96^3-class to 192x192x120) on the
+    paper-scale scanner; served: 5-iteration chains mixing the tiny
+    configuration, the paper-scale torso and batched-style torsos."""
+    rng = np.random.default_rng(2025)
+    lo, hi = 6.0, 9.0
+    out = []
+    if not served:
+        dims = W.batched_phantom_dims(a.requests)
+        for i, d in enumerate(dims):
+            n = int(a.budget_scale * 10 ** rng.uniform(lo, hi))
+            out.append({"kind": "torso", "dims": d, "seed": 100 + i, "n": max(n, 1000), "chain": i, "it": 0})
+        return out
+    for c in range(a.requests):
+        kind = ["tiny", "paper", "torso"][c % 3]
+        n = max(int(a.budget_scale * 10 ** rng.uniform(lo, hi)), 1000)
+        d = W.batched_phantom_dims(1, seed=500 + c)[0]
+        for it in range(5):
+            out.append({"kind": kind, "dims": d, "seed": 1000 * c + it, "n": n, "chain": c, "it": it})
+    return out
+
+
+def run_requests(a):
+    import threading
+    import torch
+    import paper_2509_05047_gb300 as psc
+    from paper_2509_05047_gb300 import build as B
+    B.build()
+    served = a.mode == "served"
+    dev = torch.device("cuda", 0)
+    mats = W.standard_materials()
+    sc_tiny, sc_paper = W.scanner_tiny(), W.scanner_signa()
+    mix = _request_mix(a, served)
+    phantoms = {}
+    for r in mix:
+        key = (r["kind"], r["dims"], r["chain"])
+        if key not in phantoms:
+            if r["kind"] == "tiny":
+                phantoms[key] = W.phantom_water_cylinder()
+            elif r["kind"] == "paper":
+                phantoms[key] = W.phantom_torso()
+            else:
+                phantoms[key] = W.phantom_random_torso(7 + r["chain"], r["dims"],
+                                                        W.batched_phantom_voxel(r["dims"]))
+    rng = np.random.default_rng(3)
+    for r in mix:     # each chain iteration brings a new activity image
+        ph = phantoms[(r["kind"], r["dims"], r["chain"])]
+        r["activity"] = (ph.activity * rng.uniform(0.7, 1.3, ph.activity.shape)).astype(np.float32)
+    sigma = (2.0, 2.0, 2.0)
+
+    # accumulators and resident objects share a 140 GB budget (three paper-scale
+    # accumulators), the rest of HBM holds outputs and the smoothing buffer
+    ctx = psc.psc_create(0, int(140e9))
+    s_tiny = psc.psc_load_scanner(ctx, psc.scanner_desc(sc_tiny))
+    s_paper = psc.psc_load_scanner(ctx, psc.scanner_desc(sc_paper))
+    m_id = psc.psc_load_materials(ctx, psc.materials_desc(mats).desc)
+    l_tiny = psc.psc_load_lut(ctx, psc.lut_desc(W.lut_tiny(sc_tiny)).desc)
+    l_paper = psc.psc_load_lut(ctx, psc.lut_desc(W.lut_signa(sc_paper)).desc)
+    sn_tiny = psc.psc_load_sinogram(ctx, s_tiny, W.sensitivity_uniform(sc_tiny.lor_shape, seed=1), True)
+    sn_paper = psc.psc_load_sinogram(ctx, s_paper, W.sensitivity_uniform(sc_paper.lor_shape, seed=1), True)
+    scan = {"tiny": (s_tiny, l_tiny, sn_tiny, sc_tiny)}
+    for k in ("paper", "torso"):
+        scan[k] = (s_paper, l_paper, sn_paper, sc_paper)
+    outs = {"tiny": torch.empty(sc_tiny.shape, dtype=torch.float64, device=dev),
+            "paper": torch.empty(sc_paper.shape, dtype=torch.float64, device=dev)}
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    total_h = sum(r["n"] for r in mix)
+
+    # ---- plain: one request after the other, cold residency ----
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_lat = []
+    for r in mix:
+        ts = time.perf_counter()
+        s_id, l_id, sn_id, sc = scan[r["kind"]]
+        ph = phantoms[(r["kind"], r["dims"], r["chain"])]
+        desc = psc.phantom_desc(W.Phantom(ph.dims, ph.voxel, ph.origin, ph.material, ph.density, r["activity"]))
+        p_id = psc.psc_load_phantom(ctx, desc.desc, m_id)
+        acc = psc.psc_acc_create(ctx, s_id)
+        psc.psc_simulate(ctx, psc.sim_args(r["seed"], 0, r["n"], s_id, p_id, acc, lut=l_id), stream=stream)
+        out = outs["tiny" if r["kind"] == "tiny" else "paper"]
+        psc.psc_finalize(ctx, psc.finalize_args(acc, sens=sn_id, sigma=sigma, scale=1.0 / r["n"]), out, stream)
+        torch.cuda.synchronize()
+        psc.psc_unload(ctx, acc)
+        psc.psc_unload(ctx, p_id)
+        plain_lat.append(time.perf_counter() - ts)
+    t_plain = time.perf_counter() - t0
+
+    # ---- served: resident phantoms, request server, arrivals ----
+    del outs
+    torch.cuda.empty_cache()
+    pids = {key: psc.psc_load_phantom(ctx, psc.phantom_desc(ph).desc, m_id) for key, ph in phantoms.items()}
+    n_out = a.max_active + 2
+    pool = {"tiny": [torch.empty(sc_tiny.shape, dtype=torch.float64, device=dev) for _ in range(n_out)],
+            "paper": [torch.empty(sc_paper.shape, dtype=torch.float64, device=dev) for _ in range(2)]}
+    free_out = {k: list(range(len(v))) for k, v in pool.items()}
+    torch.cuda.synchronize()
+    lock = threading.Lock()
+    cond = threading.Condition(lock)
+    psc.psc_server_start(ctx, max_active=a.max_active, epoch_histories=int(2e8), min_slice=65536)
+    lat, chain_next = [], {}
+    arrivals = np.cumsum(np.random.default_rng(4).exponential(1.0 / a.rate, size=len(mix))) if served \
+        else np.zeros(len(mix))
+    by_chain = {}
+    for i, r in enumerate(mix):
+        by_chain.setdefault(r["chain"], []).append(i)
+    t0 = time.perf_counter()
+
+    def take_out(kind):
+        k = "tiny" if kind == "tiny" else "paper"
+        with cond:
+            while not free_out[k]:
+                cond.wait()
+            return k, free_out[k].pop()
+
+    def give_out(k, j):
+        with cond:
+            free_out[k].append(j)
+            cond.notify_all()
+
+    def chain_worker(c, first_arrival):
+        ids = by_chain[c]
+        wait = first_arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        for i in ids:      # the next iteration is issued when the previous estimate is back
+            r = mix[i]
+            s_id, l_id, sn_id, sc = scan[r["kind"]]
+            k, j = take_out(r["kind"])
+            ts = time.perf_counter()
+            t = psc.psc_submit(ctx, psc.request(s_id, pids[(r["kind"], r["dims"], r["chain"])], pool[k][j],
+                                                r["n"], r["seed"], lut=l_id, sens=sn_id, sigma=sigma,
+                                                scale=1.0 / r["n"], activity=r["activity"]))
+            psc.psc_wait(ctx, t)
+            lat.append(time.perf_counter() - ts)
+            give_out(k, j)
+
+    threads = []
+    starts = arrivals[[by_chain[c][0] for c in sorted(by_chain)]] if served else np.zeros(len(by_chain))
+    for c, st in zip(sorted(by_chain), starts):
+        th = threading.Thread(target=chain_worker, args=(c, float(st)))
+        th.start()
+        threads.append(th)
+    for th in threads:
+        th.join()
+    t_served = time.perf_counter() - t0
+    psc.psc_server_stop(ctx)
+    psc.psc_destroy(ctx)
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
+    return {"mode": a.mode, "requests": len(mix), "histories": total_h,
+            "plain": {"seconds": t_plain, "histories_per_s": total_h / t_plain,
+                      "p50_latency_s": pct(plain_lat, 50), "p99_latency_s": pct(plain_lat, 99)},
+            "served": {"seconds": t_served, "histories_per_s": total_h / t_served,
+                       "p50_latency_s": pct(lat, 50), "p99_latency_s": pct(lat, 99),
+                       "max_active": a.max_active, "arrival_rate_per_s": a.rate if served else None},
+            "speedup": t_plain / t_served,
+            "note": "served results are bit-identical to the same requests alone (tests/test_gpu_server.py)"}
+
+
 def main():
     a = parse()
+    if a.mode in ("batched", "served"):
+        print(json.dumps(run_requests(a)))
+        return
     if a.mode == "precision":
         print(json.dumps(run_precision(a)))
         return

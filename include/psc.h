@@ -230,6 +230,57 @@ int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t n_crystals,
                         double scale, int32_t sens_first, double* out, psc_stream stream);
 /* Free one object. */
 int psc_unload(psc_ctx* ctx, int32_t id);
+/* Voxel count of a loaded phantom (negative PSC_E* code on error). */
+int64_t psc_phantom_voxels(psc_ctx* ctx, int32_t phantom);
+
+/* ---- Request server (continuous batching) -------------------------------
+ * One scatter estimate per request, as issued by each iteration of the joint
+ * activity/scatter estimation (Sec. 2.3.3): simulate n_histories of a
+ * resident phantom (optionally with a new activity image), then finalize
+ * into the caller's device buffer.  A server thread admits requests when an
+ * accumulator for their scanner fits the context's memory budget, runs every
+ * active request's next slice of histories in one batched launch per epoch
+ * (requests that arrive meanwhile join at the next epoch), and finalizes
+ * finished requests on a second stream.  Each result is the same as when the
+ * request runs alone. */
+typedef struct {
+  int32_t scanner, phantom, lut;   /* resident objects (lut 0: none) */
+  uint64_t seed, first_history, n_histories;
+  int32_t sens, norm, smooth;      /* as psc_finalize_args */
+  double sigma[3];
+  double scale;
+  int32_t sens_first;
+  double* out;                     /* device f64, the scanner's sinogram size; written on the
+                                      server's streams, so no other work may be pending on it */
+  const float* activity;           /* host [n_vox] new activity image, copied at submit; NULL keeps */
+} psc_request;
+
+typedef struct {
+  int32_t max_active;              /* requests simulating at once */
+  uint64_t epoch_histories;        /* histories per epoch, shared by the active requests */
+  uint64_t min_slice;              /* smallest per-request slice of an epoch (0: 65536) */
+} psc_server_config;
+
+enum { PSC_REQ_WAITING = 0, PSC_REQ_ACTIVE = 1, PSC_REQ_FINALIZING = 2, PSC_REQ_DONE = 3,
+       PSC_REQ_FAILED = 4 };
+
+typedef struct {
+  int32_t state;                   /* PSC_REQ_* */
+  int32_t error;                   /* PSC_E* code of a failed request */
+  double t_submit, t_start, t_done;  /* seconds since the server started */
+} psc_request_status;
+
+int psc_server_start(psc_ctx* ctx, const psc_server_config* cfg);
+/* Finish every submitted request, then stop the server thread. */
+int psc_server_stop(psc_ctx* ctx);
+int psc_submit(psc_ctx* ctx, const psc_request* req, uint64_t* ticket);
+int psc_poll(psc_ctx* ctx, uint64_t ticket, psc_request_status* status);
+/* Block until the request is done (PSC_OK), failed (its error code) or
+ * timeout_us microseconds have passed (PSC_ETIMEOUT). */
+int psc_wait(psc_ctx* ctx, uint64_t ticket, int64_t timeout_us);
+/* Bytes of device memory held by the context's objects. */
+uint64_t psc_resident_bytes(const psc_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

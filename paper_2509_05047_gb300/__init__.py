@@ -90,6 +90,26 @@ class FinalizeArgs(C.Structure):
                 ("sens_first", C.c_int32)]
 
 
+class Request(C.Structure):
+    _fields_ = [("scanner", C.c_int32), ("phantom", C.c_int32), ("lut", C.c_int32),
+                ("seed", C.c_uint64), ("first_history", C.c_uint64), ("n_histories", C.c_uint64),
+                ("sens", C.c_int32), ("norm", C.c_int32), ("smooth", C.c_int32),
+                ("sigma", C.c_double * 3), ("scale", C.c_double), ("sens_first", C.c_int32),
+                ("out", C.c_void_p), ("activity", C.c_void_p)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("epoch_histories", C.c_uint64),
+                ("min_slice", C.c_uint64)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+PSC_REQ_WAITING, PSC_REQ_ACTIVE, PSC_REQ_FINALIZING, PSC_REQ_DONE, PSC_REQ_FAILED = range(5)
+
 # exported entry points: name -> (restype, argtypes)
 _P, _I32, _U64 = C.c_void_p, C.c_int32, C.c_uint64
 SIGNATURES = {
@@ -114,6 +134,12 @@ SIGNATURES = {
                                       C.c_double, _I32, _P, _P]),
     "psc_unload": (C.c_int, [_P, _I32]),
     "psc_resident_bytes": (_U64, [_P]),
+    "psc_phantom_voxels": (C.c_int64, [_P, _I32]),
+    "psc_server_start": (C.c_int, [_P, C.POINTER(ServerConfig)]),
+    "psc_server_stop": (C.c_int, [_P]),
+    "psc_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "psc_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(RequestStatus)]),
+    "psc_wait": (C.c_int, [_P, C.c_uint64, C.c_int64]),
 }
 
 _lib = None
@@ -268,6 +294,58 @@ def psc_finalize_static(acc, n_rings, n_crystals, n_rad, n_tof, out, sens=None, 
 
 def psc_unload(ctx, obj):
     _check(lib().psc_unload(ctx, obj))
+
+
+def psc_phantom_voxels(ctx, phantom):
+    n = lib().psc_phantom_voxels(ctx, phantom)
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
+def psc_server_start(ctx, max_active=4, epoch_histories=200_000_000, min_slice=0):
+    _check(lib().psc_server_start(ctx, C.byref(ServerConfig(max_active, epoch_histories, min_slice))))
+
+
+def psc_server_stop(ctx):
+    _check(lib().psc_server_stop(ctx))
+
+
+def psc_submit(ctx, req: Request):
+    t = C.c_uint64()
+    _check(lib().psc_submit(ctx, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def psc_poll(ctx, ticket):
+    st = RequestStatus()
+    _check(lib().psc_poll(ctx, ticket, C.byref(st)))
+    return {"state": st.state, "error": st.error, "t_submit": st.t_submit,
+            "t_start": st.t_start, "t_done": st.t_done}
+
+
+def psc_wait(ctx, ticket, timeout_us=-1):
+    """Wait for a request; timeout_us < 0 waits without bound (in 1 s slices
+    of the bounded library wait)."""
+    if timeout_us >= 0:
+        _check(lib().psc_wait(ctx, ticket, timeout_us))
+        return
+    while True:
+        rc = lib().psc_wait(ctx, ticket, 1_000_000)
+        if rc != PSC_ETIMEOUT:
+            _check(rc)
+            return
+
+
+def request(scanner, phantom, out, n_histories, seed, lut=0, first=0, sens=0, norm=0, sigma=None,
+            scale=1.0, sens_first=False, activity=None):
+    act = None if activity is None else np.ascontiguousarray(activity, dtype=np.float32)
+    s = (C.c_double * 3)(*(sigma if sigma is not None else (0.0, 0.0, 0.0)))
+    r = Request(scanner, phantom, lut, seed, first, n_histories, sens, norm,
+                1 if sigma is not None else 0, s, scale, 1 if sens_first else 0, _ptr(out),
+                None if act is None else act.ctypes.data)
+    r._keep = (act,)
+    return r
 
 
 # ---------------------------------------------------------------------------

@@ -486,6 +486,12 @@ int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* d, int32_t materials,
   return PSC_OK;
 }
 
+int64_t psc_phantom_voxels(psc_ctx* ctx, int32_t phantom) {
+  if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
+  GET(PhantomObj, ph, phantom, kPhantomObj);
+  return ph->n_vox;
+}
+
 int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity) {
   if (!ctx || !activity) return fail(PSC_EINVAL, "NULL argument");
   GET(PhantomObj, ph, phantom, kPhantomObj);

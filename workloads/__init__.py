@@ -324,6 +324,12 @@ def phantom_random_torso(seed, dims, voxel=(3.0, 3.0, 3.0)):
     return _finish(dims, voxel, mat, dens, act)
 
 
+def batched_phantom_voxel(dims, fov_mm=400.0):
+    """Transaxial voxel that keeps an n x n grid's corners inside a 311.8 mm
+    detector radius (3 mm up to 133 voxels, then fov_mm / n); 2.78 mm axially."""
+    return (min(3.0, fov_mm / dims[0]), min(3.0, fov_mm / dims[1]), 2.78)
+
+
 def batched_phantom_dims(n=32, seed=11):
     """Uneven phantom sizes from 96x96x64 up to 192x192x120 voxels."""
     rng = np.random.default_rng(seed)
