@@ -120,6 +120,15 @@ OPS_PER_TRY = 15
 OPS_PER_INTERACTION = 45
 OPS_PER_DETECTION = 110
 OPS_PER_HISTORY = 60
+# DRAM bytes (read + write) per history of the transport kernel, from an ncu
+# capture of the same kernel on the paper-scale torso with the TOF axis
+# folded to one bin (the full 43.8 GB accumulator is too large to capture);
+# the traffic is the binned atomics and LUT misses, so it scales with the
+# histories of a launch
+TRANSPORT_DRAM_BYTES_PER_HISTORY = 112.49e6 / 2e7
+# algorithmic HBM bytes per bin of the smoothing finalize: radial 8 + 4,
+# view 4 + 4, axial 4 + 8 (per-LOR sensitivity reads are 8 / n_tof more)
+FINALIZE_BYTES_PER_BIN = 32
 
 
 def transport_ops(st):
@@ -248,9 +257,16 @@ def run_native(a):
     ops = transport_ops(st)
     achieved = ops / (kern_ms / 1e3)
     roofline = {"bound": "alu", "achieved": round(achieved / 1e9, 1), "peak": round(peak_ops / 1e9, 1),
-                "unit": "Gop/s", "frac": round(achieved / peak_ops, 4), "traffic": None,
+                "unit": "Gop/s", "frac": round(achieved / peak_ops, 4),
+                "traffic": int(TRANSPORT_DRAM_BYTES_PER_HISTORY * n),
                 "kernel": "psc::transport_kernel<0>", "kernel_ms": round(kern_ms, 3),
                 "peak_source": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)"}
+    # the three smoothing passes together, against the measured copy bandwidth
+    fin_gbs = FINALIZE_BYTES_PER_BIN * sc.n_bins / (phase[2] / 1e3) / 1e9
+    finalize_roofline = {"bound": "hbm", "achieved": round(fin_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(fin_gbs / peaks["hbm_gbs"], 4), "traffic": None,
+                         "kernels": "psc::smooth_{radial,view,axial}_kernel", "ms": round(float(phase[2]), 3),
+                         "peak_source": f"{src} copy bandwidth"}
     workload = WORKLOAD if not (a.rings or a.tof_bins) else \
         f"profiling case: {WORKLOAD} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -259,7 +275,7 @@ def run_native(a):
            "config": {"workload": workload, "histories_per_step": n, "global_batch": world * n,
                       "l2": "inputs larger than L2 (43.8 GB accumulator + 43.8 GB output streamed every step)",
                       "parallelism": f"replicas{world}"},
-           "roofline": roofline, "clocks": clocks, "e2e": e2e,
+           "roofline": roofline, "finalize_roofline": finalize_roofline, "clocks": clocks, "e2e": e2e,
            "gpu_launches": 4 * a.steps,
            "phases_ms": {"acc_zero": round(float(phase[0]), 3), "transport": round(float(phase[1]), 3),
                          "finalize": round(float(phase[2]), 3)},

@@ -204,7 +204,10 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* args, psc_stats* stats, psc_s
 int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
                        psc_stream stream);
 /* Scatter estimate = acc * scale * 2^-32, [x norm -> smooth -> / norm],
- * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size). */
+ * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size).
+ * With smoothing, out also serves as the first pass's FP32 working buffer
+ * until the last pass overwrites it.  Smoothing supports up to 255 rings
+ * and (2 n_rings - 1) * n_crystals / 2 <= 65535, else PSC_EINVAL. */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
 /* Allocation-free variant of psc_finalize for callers that cannot allocate

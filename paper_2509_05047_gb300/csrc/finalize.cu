@@ -7,31 +7,40 @@
 // c = scale * 2^-32 (the operation order of the definition, so the product
 // is exact to the last bit).
 //
-// With smoothing three passes, each reading and writing every bin once
-// through a shared-memory tile that holds whole lines of the smoothed axis
-// plus a reflected halo of K rows on each side (so the inner loop has no
-// boundary logic and no halo is re-read from HBM):
-//   A  radial: acc (int64) -> FP32 tile per (plane, view) line -> scratch
-//   B  view:   scratch in place, tile (all views) x (column chunk)
-//   C  axial:  scratch -> tile (planes of one ring-difference segment) x
-//              (column chunk) -> FP64 epilogue (x 1/norm, x sens) -> out
-// Each thread produces NB consecutive outputs along the smoothed axis from a
-// register sliding window (NB + 2K shared-memory loads for NB outputs), with
-// the truncation radius K a template parameter for K <= kMaxTemplK.
-// Kernels are truncated at ceil(4 sigma) with weights normalised to 1; edges
-// reflect half-sample symmetrically; a plane's axial neighbours are the
-// planes of the same ring difference.
+// With smoothing three separable passes, each reading and writing every bin
+// once.  A thread owns one column of the smoothed axis and slides down it
+// with a register window: NB outputs per step from NB new loads, the 2K
+// halo rows carried over in registers, the reflected edge rows loaded by
+// index.  Loads and stores of a warp cover 32 consecutive bins of the
+// innermost axes, so every access is coalesced; no shared memory and no
+// barriers are needed, and enough warps are resident to keep HBM busy.
+//   A  radial: acc (int64) -> FP32, columns (plane, view, tof) along rad,
+//              into the first half of the output buffer (used as scratch)
+//   B  view:   that -> FP32 working sinogram, columns (plane, rad, tof)
+//   C  axial:  working sinogram -> FP64 epilogue (x 1/norm, x sens) -> out,
+//              columns (segment, view, rad, tof) along the segment's planes
+// No pass writes what it reads.  Kernels are truncated at ceil(4 sigma) with
+// weights normalised to 1 and zero-padded to the instantiated radius KT
+// (exact for K <= 8, then 10, 12, 16, 20, 24; a per-tap loop beyond), so the
+// FMA chain is the same for every KT >= K; edges reflect half-sample
+// symmetrically; a plane's axial neighbours are the planes of the same ring
+// difference.
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 
+#include "psc.h"
 #include "psc_internal.h"
 
 namespace psc {
 
-constexpr int NB = 8;            // outputs per thread along the smoothed axis
-constexpr int kMaxTemplK = 12;   // template-specialised truncation radii 1..12
-constexpr int kMaxRings = 128;   // rings per scanner for the axial pass
+constexpr int NB = 8;            // outputs per window step along the smoothed axis
+constexpr int kSmoothThreads = 256;
 
+// half-sample symmetric reflection of row m into [0, n), periodic beyond
+// one reflection (only axes shorter than the kernel get there)
 __device__ __forceinline__ int reflect(int m, int n) {
+  if (m >= -n && m < 2 * n) return m < 0 ? -m - 1 : (m >= n ? 2 * n - 1 - m : m);
   const int p = 2 * n;
   m %= p;
   if (m < 0) m += p;
@@ -56,6 +65,12 @@ __device__ __forceinline__ double at(const double* a, long long i) { return __ld
 // to the hardware instruction.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kMant52 = (1ull << 52) - 1;
+
+// the rare operands outside the normal range go to the FP64 hardware; kept
+// out of line so the compiler never if-converts them into the common path
+__device__ __noinline__ double hw_f32_to_f64(float f) { return (double)f; }
+__device__ __noinline__ double hw_fmul_fd(float x, double b) { return (double)x * b; }
+__device__ __noinline__ double hw_dmul(double a, double b) { return a * b; }
 
 // index of the highest / lowest set bit of a non-zero 64-bit value, from the
 // 32-bit bit-scan instructions
@@ -107,7 +122,7 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned b = (unsigned)__float_as_int(f);
   const unsigned ef = (b >> 23) & 0xffu;
   if ((b & 0x7fffffffu) == 0) return (b >> 31) ? -0.0 : 0.0;
-  if (ef == 0 || ef == 0xffu) return (double)f;
+  if (ef == 0 || ef == 0xffu) return hw_f32_to_f64(f);
   return __longlong_as_double(((unsigned long long)(b >> 31) << 63) |
                               ((unsigned long long)(ef - 127 + 1023) << 52) |
                               ((unsigned long long)(b & 0x7fffffu) << 29));
@@ -120,7 +135,7 @@ __device__ __forceinline__ double fmul_fd(float x, double b) {
   const unsigned long long sign = ((unsigned long long)(xb >> 31) << 63) ^ (ub & (1ull << 63));
   const int ex = (int)((xb >> 23) & 0xffu), eb = (int)((ub >> 52) & 0x7ff);
   if ((xb << 1) == 0 || (ub << 1) == 0) return __longlong_as_double((long long)sign);
-  if (ex == 0 || ex == 0xff || eb == 0 || eb == 0x7ff) return (double)x * b;
+  if (ex == 0 || ex == 0xff || eb == 0 || eb == 0x7ff) return hw_fmul_fd(x, b);
   const unsigned long long mx = (xb & 0x7fffffu) | 0x800000u;          // 24 bits
   const unsigned long long mb = (ub & kMant52) | (1ull << 52);         // 53 bits
   // P = mx * mb in [2^75, 2^77) = hi 2^32 + lo; T = P >> 13 in [2^62, 2^64)
@@ -131,7 +146,7 @@ __device__ __forceinline__ double fmul_fd(float x, double b) {
   const int top = (int)(T >> 63);
   int e = ex + eb - 127 + top;
   const unsigned long long m = rne_shift(T, 10 + top, sticky, 53, e);
-  if (e <= 0 || e >= 0x7ff) return (double)x * b;
+  if (e <= 0 || e >= 0x7ff) return hw_fmul_fd(x, b);
   return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
 }
 
@@ -142,7 +157,7 @@ __device__ __forceinline__ double dmul(double a, double b) {
   const unsigned long long sign = (ua ^ ub) & (1ull << 63);
   const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
   if (((ua << 1) == 0) || ((ub << 1) == 0)) return __longlong_as_double((long long)sign);
-  if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return a * b;
+  if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return hw_dmul(a, b);
   const unsigned long long ma = (ua & kMant52) | (1ull << 52), mb = (ub & kMant52) | (1ull << 52);
   // ma * mb in [2^104, 2^106): top 64 bits of (ma * mb) << 22, sticky below
   const unsigned long long hi = __umul64hi(ma << 11, mb << 11);
@@ -151,7 +166,7 @@ __device__ __forceinline__ double dmul(double a, double b) {
   const int top = (int)(hi >> 63);
   e += top;
   const unsigned long long m = rne_shift(hi, 10 + top, sticky, 53, e);
-  if (e <= 0 || e >= 0x7ff) return a * b;
+  if (e <= 0 || e >= 0x7ff) return hw_dmul(a, b);
   return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
 }
 
@@ -172,196 +187,163 @@ __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_consta
   }
 }
 
+
+
 // ---------------------------------------------------------------------------
-// the convolution of one thread's NB outputs along a tile column
+// the sliding window down one column of n rows; row r of the source is
+// src[r * stride] (rows outside [0, n) reflect).  cvt(raw, r) -> float;
+// store(r, value).  Each output is the FMA chain sum_j g[j] * x[o - KT + j],
+// j = 0 .. 2 KT, in increasing j.  The NB loads of a step are issued before
+// any of them is converted, and rows are reflected only in the edge steps.
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void conv_slide(const float* col, int ld, const float* gs, float (&o)[NB]) {
-  float g[2 * K + 1];
+using Weights = float[2 * kMaxSmoothRadius + 1];
+
+template <int KT, class In, class Cvt, class Store>
+__device__ __forceinline__ void slide(const In* __restrict__ src, long long stride, int n, const Weights& g,
+                                      Cvt cvt, Store store) {
+  float w[NB + 2 * KT];
 #pragma unroll
-  for (int j = 0; j <= 2 * K; ++j) g[j] = gs[j];
+  for (int j = 0; j < 2 * KT; ++j) {
+    const int r = reflect(j - KT, n);
+    w[j] = cvt(__ldg(src + r * stride), r);
+  }
+  for (int o0 = 0; o0 < n; o0 += NB) {
+    In raw[NB];
+    int rr[NB];
+    if (o0 + KT + NB <= n) {
+      const In* p = src + (long long)(o0 + KT) * stride;
 #pragma unroll
-  for (int b = 0; b < NB; ++b) o[b] = 0.0f;
+      for (int q = 0; q < NB; ++q) {
+        raw[q] = __ldg(p + q * stride);
+        rr[q] = o0 + KT + q;
+      }
+    } else {
 #pragma unroll
-  for (int m = 0; m < NB + 2 * K; ++m) {
-    const float x = col[m * ld];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int j = m - b;
-      if (j >= 0 && j <= 2 * K) o[b] = fmaf(g[j], x, o[b]);
+      for (int q = 0; q < NB; ++q) {
+        rr[q] = reflect(o0 + KT + q, n);
+        raw[q] = __ldg(src + rr[q] * stride);
+      }
     }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) w[2 * KT + q] = cvt(raw[q], rr[q]);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      float s = 0.0f;
+#pragma unroll
+      for (int j = 0; j <= 2 * KT; ++j) s = fmaf(g[j], w[q + j], s);
+      if (o0 + q < n) store(o0 + q, s);
+    }
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) w[j] = w[NB + j];
   }
 }
 
-__device__ __forceinline__ void conv_generic(const float* col, int ld, const float* gs, int K, float (&o)[NB]) {
-#pragma unroll
-  for (int b = 0; b < NB; ++b) o[b] = 0.0f;
-  for (int j = 0; j <= 2 * K; ++j) {
-    const float gj = gs[j];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) o[b] = fmaf(gj, col[(b + j) * ld], o[b]);
+// radii above the largest instantiated window: one load per tap
+template <class In, class Cvt, class Store>
+__device__ __forceinline__ void slide_generic(const In* __restrict__ src, long long stride, int n, int K,
+                                              const Weights& g, Cvt cvt, Store store) {
+  for (int o = 0; o < n; ++o) {
+    float s = 0.0f;
+    for (int j = 0; j <= 2 * K; ++j) {
+      const int r = reflect(o - K + j, n);
+      s = fmaf(g[j], cvt(__ldg(src + r * stride), r), s);
+    }
+    store(o, s);
   }
 }
 
-template <int K>
-__device__ __forceinline__ void conv(const float* col, int ld, const float* gs, int Kr, float (&o)[NB]) {
-  if (K >= 0) conv_slide<(K >= 0 ? K : 0)>(col, ld, gs, o);
-  else conv_generic(col, ld, gs, Kr, o);
+template <int KT, class In, class Cvt, class Store>
+__device__ __forceinline__ void slide_any(const In* src, long long stride, int n, int K, const Weights& g, Cvt cvt,
+                                          Store store) {
+  if constexpr (KT >= 0) slide<KT>(src, stride, n, g, cvt, store);
+  else slide_generic(src, stride, n, K, g, cvt, store);
 }
 
-// rows of a tile: core n rounded up to NB, plus K halo rows on each side
-__host__ __device__ inline int tile_rows(int n, int K) { return (n + NB - 1) / NB * NB + 2 * K; }
-
 // ---------------------------------------------------------------------------
-// pass A: radial.  One CTA per (plane, view) line of R x T values.
+// pass A: radial.  grid (ceil(V T / 256), planes); a thread owns the column
+// (plane, view, tof) and slides along rad.  acc * c [x sens] [x norm] in
+// FP32, written as FP32 into the first half of the output buffer.
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(256) smooth_radial_kernel(const __grid_constant__ FinParams P) {
-  extern __shared__ float ext[];           // [tile_rows(R, K)][T]
-  __shared__ float gs[2 * kMaxSmoothRadius + 1];
-  const int Kr = K >= 0 ? K : P.K[0];
-  for (int j = threadIdx.x; j <= 2 * Kr; j += blockDim.x) gs[j] = P.g[0][j];
-  const long long line = blockIdx.x;       // plane * V + view
+template <int KT>
+__global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __grid_constant__ FinParams P) {
+  const int VT = P.V * P.T;
+  const int c = blockIdx.x * kSmoothThreads + threadIdx.x;
+  if (c >= VT) return;
+  const int v = (int)fdiv((unsigned)c, P.magic_T), t = c - v * P.T;
+  const long long line = (long long)blockIdx.y * P.V + v;
   const int R = P.R, T = P.T;
-  const int rows = tile_rows(R, Kr);
-  const long long base = line * (long long)R * T;
+  const long long base = line * R * T + t;  // bin of (line, r = 0, t)
   const float cf = (float)P.c;
-  for (int i = threadIdx.x; i < rows * T; i += blockDim.x) {
-    const int e = (int)fdiv((unsigned)i, P.magic_T), t = i - e * T;
-    const int s = e - Kr;
-    float x = 0.0f;
-    if (s < R + Kr) {
-      const int r = (s >= 0 && s < R) ? s : reflect(s, R);
-      const long long bin = base + (long long)r * T + t;
-      x = i64_to_f32(__ldg(P.acc + bin)) * cf;
-      if (P.sens_first && P.sens) x *= (float)at(P.sens, P.sens_per_lor ? line * R + r : bin);
-      if (P.norm) x *= (float)at(P.norm, P.norm_per_lor ? line * R + r : bin);
+  const bool per_bin_factor = (P.sens_first && P.sens) || P.norm;
+  float* dst = reinterpret_cast<float*>(P.out) + base;
+  auto cvt = [&](long long q, int r) {
+    float x = i64_to_f32(q) * cf;
+    if (per_bin_factor) {
+      const long long bin = base + (long long)r * T, lor = line * R + r;
+      if (P.sens_first && P.sens) x *= (float)at(P.sens, P.sens_per_lor ? lor : bin);
+      if (P.norm) x *= (float)at(P.norm, P.norm_per_lor ? lor : bin);
     }
-    ext[i] = x;
-  }
-  __syncthreads();
-  const int nrb = (R + NB - 1) / NB;
-  for (int i = threadIdx.x; i < nrb * T; i += blockDim.x) {
-    const int rb = (int)fdiv((unsigned)i, P.magic_T), t = i - rb * T;
-    float o[NB];
-    conv<K>(ext + rb * NB * T + t, T, gs, Kr, o);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int r = rb * NB + b;
-      if (r < R) P.scratch[base + (long long)r * T + t] = o[b];
-    }
-  }
+    return x;
+  };
+  auto store = [&](int r, float y) { dst[r * T] = y; };
+  slide_any<KT>(P.acc + base, T, R, P.K[0], P.g[0], cvt, store);
 }
 
 // ---------------------------------------------------------------------------
-// pass B: view.  CTA per (plane, chunk of CH columns of the (rad, tof)
-// plane); the tile holds every view of that chunk.  In place on the scratch
-// buffer: a CTA reads its whole tile before writing, and tiles are disjoint.
+// pass B: view.  grid (ceil(R T / 256), planes); a thread owns the column
+// (plane, rad, tof) and slides along view.
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(256) smooth_view_kernel(const __grid_constant__ FinParams P) {
-  extern __shared__ float ext[];           // [tile_rows(V, K)][CH]
-  __shared__ float gs[2 * kMaxSmoothRadius + 1];
-  const int Kr = K >= 0 ? K : P.K[1];
-  for (int j = threadIdx.x; j <= 2 * Kr; j += blockDim.x) gs[j] = P.g[1][j];
-  const int V = P.V, I = P.R * P.T, CH = P.chunk_view, sh = P.chunk_view_log2;
-  const int n_chunks = (I + CH - 1) / CH;
-  const long long plane = blockIdx.x / n_chunks;
-  const int j0 = (blockIdx.x % n_chunks) * CH;
-  const int cw = min(CH, I - j0);
-  const int rows = tile_rows(V, Kr);
-  const long long base = plane * V * (long long)I + j0;
-  for (int i = threadIdx.x; i < rows * CH; i += blockDim.x) {
-    const int e = i >> sh, c = i & (CH - 1);
-    const int s = e - Kr;
-    float x = 0.0f;
-    if (c < cw && s < V + Kr) {
-      const int v = (s >= 0 && s < V) ? s : reflect(s, V);
-      x = P.scratch[base + (long long)v * I + c];
-    }
-    ext[i] = x;
-  }
-  __syncthreads();
-  const int nvb = (V + NB - 1) / NB;
-  for (int i = threadIdx.x; i < nvb * CH; i += blockDim.x) {
-    const int vb = i >> sh, c = i & (CH - 1);
-    if (c >= cw) continue;
-    float o[NB];
-    conv<K>(ext + vb * NB * CH + c, CH, gs, Kr, o);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int v = vb * NB + b;
-      if (v < V) P.scratch[base + (long long)v * I + c] = o[b];
-    }
-  }
+template <int KT>
+__global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __grid_constant__ FinParams P) {
+  const int I = P.R * P.T;
+  const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
+  if (i >= I) return;
+  const long long base = (long long)blockIdx.y * P.V * I + i;
+  const float* src = reinterpret_cast<const float*>(P.out) + base;
+  float* dst = P.scratch + base;
+  auto cvt = [](float x, int) { return x; };
+  auto store = [&](int v, float y) { dst[v * I] = y; };
+  slide_any<KT>(src, I, P.V, P.K[1], P.g[1], cvt, store);
 }
 
 // ---------------------------------------------------------------------------
 // pass C: axial within a ring-difference segment, then the FP64 epilogue.
-// CTA per (segment, chunk of CH columns of the (view, rad, tof) volume).
+// grid (ceil(R T / 256), segments x V); a thread owns the column (segment,
+// view, rad, tof) and slides along the segment's planes p0 + k (n_rings + 1).
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(256) smooth_axial_kernel(const __grid_constant__ FinParams P) {
-  extern __shared__ float ext[];           // [tile_rows(L, K)][CH]
-  __shared__ float gs[2 * kMaxSmoothRadius + 1];
-  __shared__ long long s_bin[kMaxRings];   // first bin of the segment's plane k
-  __shared__ long long s_lor[kMaxRings];   // first LOR of the segment's plane k
-  __shared__ int s_src[kMaxRings + 2 * kMaxSmoothRadius + NB];  // core row of tile row e (-1: pad)
-  const int Kr = K >= 0 ? K : P.K[2];
-  for (int j = threadIdx.x; j <= 2 * Kr; j += blockDim.x) gs[j] = P.g[2][j];
+template <int KT>
+__global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
+  const int I = P.R * P.T;
+  const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
+  if (i >= I) return;
   const int nr = P.n_rings;
-  const int J = P.V * P.R * P.T;
-  const int CH = P.chunk_axial, sh = P.chunk_axial_log2;
-  const int n_chunks = (J + CH - 1) / CH;
-  const int seg = blockIdx.x / n_chunks;             // 0 .. 2 nr - 2
-  const int j0 = (blockIdx.x % n_chunks) * CH;
-  const int cw = min(CH, J - j0);
-  const int d = seg - (nr - 1);                      // ring difference rb - ra
+  const int seg = blockIdx.y / P.V, v = blockIdx.y - seg * P.V;
+  const int d = seg - (nr - 1);  // ring difference rb - ra
   const int ra0 = max(0, -d);
   const int L = nr - abs(d);
-  const int rows = tile_rows(L, Kr);
+  const long long J = (long long)P.V * I;
+  const long long p0 = (long long)ra0 * (nr + 1) + d;
+  const long long bin0 = p0 * J + (long long)v * I + i;       // bin of k = 0
+  const long long bin_step = (long long)(nr + 1) * J;         // next plane of the segment
   const long long lors = (long long)P.V * P.R;
-  for (int k = threadIdx.x; k < L; k += blockDim.x) {
-    const long long plane = (long long)(ra0 + k) * nr + (ra0 + k + d);
-    s_bin[k] = plane * J;
-    s_lor[k] = plane * lors;
-  }
-  for (int e = threadIdx.x; e < rows; e += blockDim.x) {
-    const int s = e - Kr;
-    s_src[e] = s < L + Kr ? ((s >= 0 && s < L) ? s : reflect(s, L)) : -1;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < rows * CH; i += blockDim.x) {
-    const int e = i >> sh, c = i & (CH - 1);
-    const int k = s_src[e];
-    ext[i] = (c < cw && k >= 0) ? P.scratch[s_bin[k] + j0 + c] : 0.0f;
-  }
-  __syncthreads();
-  const int nkb = (L + NB - 1) / NB;
-  for (int i = threadIdx.x; i < nkb * CH; i += blockDim.x) {
-    const int kb = i >> sh, c = i & (CH - 1);
-    if (c >= cw) continue;
-    float o[NB];
-    conv<K>(ext + kb * NB * CH + c, CH, gs, Kr, o);
-    const int lor_in_plane = (int)fdiv((unsigned)(j0 + c), P.magic_T);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int k = kb * NB + b;
-      if (k >= L) break;
-      const long long bin = s_bin[k] + j0 + c;
-      const long long lor = s_lor[k] + lor_in_plane;
-      double y;
-      if (P.rnorm) {
-        y = fmul_fd(o[b], at(P.rnorm, P.norm_per_lor ? lor : bin));
-        if (!P.sens_first && P.sens) y = dmul(y, at(P.sens, P.sens_per_lor ? lor : bin));
-      } else if (!P.sens_first && P.sens) {
-        y = fmul_fd(o[b], at(P.sens, P.sens_per_lor ? lor : bin));
-      } else {
-        y = f32_to_f64(o[b]);
-      }
-      P.out[bin] = y;
+  const long long lor0 = p0 * lors + (long long)v * P.R + fdiv((unsigned)i, P.magic_T);
+  const long long lor_step = (long long)(nr + 1) * lors;
+  auto cvt = [](float x, int) { return x; };
+  auto store = [&](int k, float o) {
+    const long long bin = bin0 + k * bin_step;
+    const long long lor = lor0 + k * lor_step;
+    double y;
+    if (P.rnorm) {
+      y = fmul_fd(o, at(P.rnorm, P.norm_per_lor ? lor : bin));
+      if (!P.sens_first && P.sens) y = dmul(y, at(P.sens, P.sens_per_lor ? lor : bin));
+    } else if (!P.sens_first && P.sens) {
+      y = fmul_fd(o, at(P.sens, P.sens_per_lor ? lor : bin));
+    } else {
+      y = f32_to_f64(o);
     }
-  }
+    P.out[bin] = y;
+  };
+  slide_any<KT>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
 }
 
 // reciprocal of a normalisation sinogram, 0 where it is 0
@@ -384,29 +366,59 @@ cudaError_t launch_reciprocal(const double* a, double* r, long long n, int sms, 
   return cudaGetLastError();
 }
 
-size_t finalize_smem_radial(const FinParams& p) { return sizeof(float) * (size_t)tile_rows(p.R, p.K[0]) * p.T; }
-size_t finalize_smem_view(const FinParams& p) { return sizeof(float) * (size_t)tile_rows(p.V, p.K[1]) * p.chunk_view; }
-size_t finalize_smem_axial(const FinParams& p) { return sizeof(float) * (size_t)tile_rows(p.n_rings, p.K[2]) * p.chunk_axial; }
+// ---------------------------------------------------------------------------
+// host side: weights and window radii, launches
+// ---------------------------------------------------------------------------
+// instantiated window radii (ascending); larger K use the per-tap loop
+constexpr int kWindowRadii[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 20, 24};
 
-template <template <int> class Launcher, int K>
-static cudaError_t dispatch_k(int k, const FinParams& p, size_t smem, unsigned grid, cudaStream_t s) {
-  if constexpr (K > kMaxTemplK) {
-    return Launcher<-1>::run(p, smem, grid, s);
+int finalize_plan(FinParams& p, const double sigma[3]) {
+  if ((long long)p.n_rings * p.n_rings > 65535 || (2LL * p.n_rings - 1) * p.V > 65535)
+    return psc_set_error(PSC_EINVAL, "smoothing supports at most 65535 planes and 65535 segment views");
+  for (int ax = 0; ax < 3; ++ax) {
+    const double sg = sigma[ax];
+    if (!(sg >= 0.0) || !std::isfinite(sg)) return psc_set_error(PSC_EINVAL, "sigma[%d] must be finite and >= 0", ax);
+    const int K = sg > 0.0 ? (int)std::ceil(4.0 * sg) : 0;
+    if (K > kMaxSmoothRadius)
+      return psc_set_error(PSC_EINVAL, "sigma[%d] too large (4 sigma > %d bins)", ax, kMaxSmoothRadius);
+    double w[2 * kMaxSmoothRadius + 1], sum = 0.0;
+    for (int k = -K; k <= K; ++k) {
+      w[k + K] = K ? std::exp(-0.5 * (k / sg) * (k / sg)) : 1.0;
+      sum += w[k + K];
+    }
+    int KT = -1;
+    for (int r : kWindowRadii)
+      if (r >= K) {
+        KT = r;
+        break;
+      }
+    const int c = KT >= 0 ? KT : K;  // centre of the stored weights
+    p.K[ax] = K;
+    p.KT[ax] = KT;
+    for (int j = 0; j <= 2 * kMaxSmoothRadius; ++j) p.g[ax][j] = 0.0f;
+    for (int k = -K; k <= K; ++k) p.g[ax][c + k] = (float)(w[k + K] / sum);
+  }
+  return PSC_OK;
+}
+
+template <template <int> class Launcher, int I = 0>
+static cudaError_t dispatch_kt(int kt, const FinParams& p, dim3 grid, cudaStream_t s) {
+  constexpr int n = (int)(sizeof(kWindowRadii) / sizeof(kWindowRadii[0]));
+  if constexpr (I == n) {
+    return Launcher<-1>::run(p, grid, s);
   } else {
-    if (k == K) return Launcher<K>::run(p, smem, grid, s);
-    return dispatch_k<Launcher, K + 1>(k, p, smem, grid, s);
+    if (kt == kWindowRadii[I]) return Launcher<kWindowRadii[I]>::run(p, grid, s);
+    return dispatch_kt<Launcher, I + 1>(kt, p, grid, s);
   }
 }
 
-#define PSC_LAUNCHER(NAME, KERNEL)                                                             \
-  template <int K>                                                                             \
-  struct NAME {                                                                                \
-    static cudaError_t run(const FinParams& p, size_t smem, unsigned grid, cudaStream_t s) {    \
-      cudaError_t e = cudaFuncSetAttribute(KERNEL<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-      if (e != cudaSuccess) return e;                                                          \
-      KERNEL<K><<<grid, 256, smem, s>>>(p);                                                    \
-      return cudaGetLastError();                                                               \
-    }                                                                                          \
+#define PSC_LAUNCHER(NAME, KERNEL)                                          \
+  template <int KT>                                                         \
+  struct NAME {                                                             \
+    static cudaError_t run(const FinParams& p, dim3 grid, cudaStream_t s) { \
+      KERNEL<KT><<<grid, kSmoothThreads, 0, s>>>(p);                        \
+      return cudaGetLastError();                                            \
+    }                                                                       \
   };
 PSC_LAUNCHER(RadialL, smooth_radial_kernel)
 PSC_LAUNCHER(ViewL, smooth_view_kernel)
@@ -414,21 +426,18 @@ PSC_LAUNCHER(AxialL, smooth_axial_kernel)
 
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s) {
   cudaError_t e;
+  const unsigned planes = (unsigned)((long long)p.n_rings * p.n_rings);
   if (!p.smooth) {
     const long long J = (long long)p.V * p.R * p.T;
-    const unsigned planes = (unsigned)((long long)p.n_rings * p.n_rings);
     const long long per_plane = std::max(1LL, std::min((J + 255) / 256, 8LL * sms / (long long)planes + 1));
     finalize_plain_kernel<<<dim3((unsigned)per_plane, planes), 256, 0, s>>>(p);
     return cudaGetLastError();
   }
-  const unsigned n_lines = (unsigned)((long long)p.n_rings * p.n_rings * p.V);
-  if ((e = dispatch_k<RadialL, 1>(p.K[0] == 0 ? -1 : p.K[0], p, finalize_smem_radial(p), n_lines, s)) != cudaSuccess) return e;
+  auto blocks = [](long long n) { return (unsigned)((n + kSmoothThreads - 1) / kSmoothThreads); };
   const long long I = (long long)p.R * p.T;
-  const unsigned nb = (unsigned)((long long)p.n_rings * p.n_rings * ((I + p.chunk_view - 1) / p.chunk_view));
-  if ((e = dispatch_k<ViewL, 1>(p.K[1] == 0 ? -1 : p.K[1], p, finalize_smem_view(p), nb, s)) != cudaSuccess) return e;
-  const long long J = (long long)p.V * I;
-  const unsigned na = (unsigned)((long long)(2 * p.n_rings - 1) * ((J + p.chunk_axial - 1) / p.chunk_axial));
-  return dispatch_k<AxialL, 1>(p.K[2] == 0 ? -1 : p.K[2], p, finalize_smem_axial(p), na, s);
+  if ((e = dispatch_kt<RadialL>(p.KT[0], p, dim3(blocks((long long)p.V * p.T), planes), s)) != cudaSuccess) return e;
+  if ((e = dispatch_kt<ViewL>(p.KT[1], p, dim3(blocks(I), planes), s)) != cudaSuccess) return e;
+  return dispatch_kt<AxialL>(p.KT[2], p, dim3(blocks(I), (unsigned)((2LL * p.n_rings - 1) * p.V)), s);
 }
 
 }  // namespace psc

@@ -67,11 +67,9 @@ extern "C" int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t 
   p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
   const long long J = (long long)p.V * p.R * p.T;
   if (J * p.T >= (1LL << 32)) return psc_set_error(PSC_EOVERFLOW, "a sinogram plane is too large");
-  int sms = 0, smem_optin = 0;
+  int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaStream_t s = (cudaStream_t)stream;
-  if (p.smooth && n_rings > 128) return psc_set_error(PSC_EINVAL, "smoothing supports at most 128 rings");
   if (!p.smooth) {
     e = launch_finalize(p, sms, s);
     return e == cudaSuccess ? PSC_OK : psc_set_error(PSC_EDEVICE, "finalize: %s", cudaGetErrorString(e));
@@ -79,39 +77,18 @@ extern "C" int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t 
 
   // working memory needed: FP32 sinogram + FP64 reciprocal of norm
   const long long n_norm = norm ? (norm_per_lor ? p.n_bins / p.T : p.n_bins) : 0;
-  const size_t norm_off = (sizeof(float) * (size_t)p.n_bins + 255) / 256 * 256;
-  const size_t need = norm ? norm_off + sizeof(double) * (size_t)n_norm : sizeof(float) * (size_t)p.n_bins;
+  const size_t scr = sizeof(float) * (size_t)p.n_bins;
+  const size_t norm_off = (scr + 255) / 256 * 256;
+  const size_t need = norm ? norm_off + sizeof(double) * (size_t)n_norm : scr;
   if (need > kStaticScratchBytes)
     return psc_set_error(PSC_EOVERFLOW,
                          "sinogram needs %zu bytes of working memory; the allocation-free entry "
                          "point holds %zu (4 bytes per bin + 8 per normalisation value)",
                          need, kStaticScratchBytes);
-  for (int ax = 0; ax < 3; ++ax) {
-    const double sg = sigma[ax];
-    if (!(sg >= 0.0) || !std::isfinite(sg)) return psc_set_error(PSC_EINVAL, "sigma[%d] invalid", ax);
-    const int K = sg > 0.0 ? (int)std::ceil(4.0 * sg) : 0;
-    if (K > kMaxSmoothRadius) return psc_set_error(PSC_EINVAL, "sigma[%d] too large", ax);
-    p.K[ax] = K;
-    double w[2 * kMaxSmoothRadius + 1], sum = 0.0;
-    for (int k = -K; k <= K; ++k) {
-      w[k + K] = K ? std::exp(-0.5 * (k / sg) * (k / sg)) : 1.0;
-      sum += w[k + K];
-    }
-    for (int j = 0; j <= 2 * K; ++j) p.g[ax][j] = (float)(w[j] / sum);
+  {
+    const int rc = finalize_plan(p, sigma);
+    if (rc) return rc;
   }
-  auto pick = [](long long rows, int cap) {
-    int ch = 1, lg = 0;
-    while (ch * 2 <= cap && (long long)(ch * 2) * rows * (long long)sizeof(float) <= 48 * 1024) {
-      ch *= 2;
-      ++lg;
-    }
-    return std::make_pair(ch, lg);
-  };
-  std::tie(p.chunk_view, p.chunk_view_log2) = pick((p.V + 7) / 8 * 8 + 2 * p.K[1], 32);
-  std::tie(p.chunk_axial, p.chunk_axial_log2) = pick((p.n_rings + 7) / 8 * 8 + 2 * p.K[2], 128);
-  if (finalize_smem_radial(p) > (size_t)smem_optin || finalize_smem_view(p) > (size_t)smem_optin ||
-      finalize_smem_axial(p) > (size_t)smem_optin)
-    return psc_set_error(PSC_EINVAL, "smoothing tiles do not fit in shared memory");
 
   // set-up, once per device with that device current: the device address
   // of the working array (its name in host code is only a host stand-in)

@@ -12,7 +12,7 @@ namespace psc {
 struct FinParams {
   const long long* acc;
   double* out;
-  float* scratch;              // FP32 sinogram-sized working buffer (smoothing only)
+  float* scratch;              // FP32 working sinogram, n_bins floats (smoothing only)
   const double* sens;
   const double* norm;
   const double* rnorm;         // 1/norm, 0 where norm == 0
@@ -21,11 +21,10 @@ struct FinParams {
   long long n_bins;
   int n_rings, V, R, T;
   int smooth, sens_first;
-  int chunk_view, chunk_axial;          // column chunks (powers of two)
-  int chunk_view_log2, chunk_axial_log2;
-  unsigned magic_T;                     // ceil(2^32 / T) for exact i / T, 0 when T == 1
+  unsigned magic_T;            // ceil(2^32 / T) for exact i / T, 0 when T == 1
   int K[3];                    // truncation radius per axis (radial, view, axial)
-  float g[3][2 * kMaxSmoothRadius + 1];
+  int KT[3];                   // instantiated window radius >= K, or -1: per-tap loop
+  float g[3][2 * kMaxSmoothRadius + 1];  // weights centred on KT (on K when KT = -1), zero-padded
 };
 
 // sets the calling thread's psc_last_error() message, returns code
@@ -36,9 +35,9 @@ cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int 
                              cudaStream_t s);
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm);
 
-size_t finalize_smem_radial(const FinParams& p);
-size_t finalize_smem_view(const FinParams& p);
-size_t finalize_smem_axial(const FinParams& p);
+// smoothing weights and window radii from sigma (bins, per axis): PSC_OK,
+// or an error code with the message set
+int finalize_plan(FinParams& p, const double sigma[3]);
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s);
 cudaError_t launch_reciprocal(const double* a, double* r, long long n, int sms, cudaStream_t s);
 

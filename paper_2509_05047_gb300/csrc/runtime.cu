@@ -830,18 +830,9 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
     CK(launch_finalize(p, ctx->sms, s), "finalize");
     return PSC_OK;
   }
-  for (int ax = 0; ax < 3; ++ax) {
-    const double sg = a->sigma[ax];
-    if (!(sg >= 0.0) || !std::isfinite(sg)) return fail(PSC_EINVAL, "sigma[%d] must be finite and >= 0", ax);
-    const int K = sg > 0.0 ? (int)std::ceil(4.0 * sg) : 0;
-    if (K > kMaxSmoothRadius) return fail(PSC_EINVAL, "sigma[%d] too large (4 sigma > %d bins)", ax, kMaxSmoothRadius);
-    p.K[ax] = K;
-    double w[2 * kMaxSmoothRadius + 1], sum = 0.0;
-    for (int k = -K; k <= K; ++k) {
-      w[k + K] = K ? std::exp(-0.5 * (k / sg) * (k / sg)) : 1.0;
-      sum += w[k + K];
-    }
-    for (int j = 0; j <= 2 * K; ++j) p.g[ax][j] = (float)(w[j] / sum);
+  {
+    const int rc = finalize_plan(p, a->sigma);
+    if (rc) return rc;
   }
   if (norm) {
     p.norm = (const double*)norm->data.p;
@@ -853,28 +844,6 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
     }
     p.rnorm = (const double*)norm->recip.p;
   }
-  // tile sizes: radial lines whole; view / axial column chunks (powers of
-  // two) sized so a tile stays within 48 KB
-  p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
-  if (p.n_rings > 128) return fail(PSC_EINVAL, "smoothing supports at most 128 rings");
-  const long long J = (long long)p.V * p.R * p.T;
-  if (J * p.T >= (1LL << 32)) return fail(PSC_EOVERFLOW, "a sinogram plane of %lld bins is too large", J);
-  if (finalize_smem_radial(p) > (size_t)ctx->max_smem_optin)
-    return fail(PSC_EINVAL, "a radial line of %d x %d bins does not fit in shared memory", p.R, p.T);
-  auto pick = [](long long rows, int cap) {
-    int ch = 1, lg = 0;
-    while (ch * 2 <= cap && (long long)(ch * 2) * rows * (long long)sizeof(float) <= 48 * 1024) {
-      ch *= 2;
-      ++lg;
-    }
-    return std::make_pair(ch, lg);
-  };
-  const long long rows_v = (p.V + 7) / 8 * 8 + 2 * p.K[1];
-  const long long rows_a = (p.n_rings + 7) / 8 * 8 + 2 * p.K[2];
-  std::tie(p.chunk_view, p.chunk_view_log2) = pick(rows_v, 32);
-  std::tie(p.chunk_axial, p.chunk_axial_log2) = pick(rows_a, 128);
-  if (finalize_smem_view(p) > (size_t)ctx->max_smem_optin || finalize_smem_axial(p) > (size_t)ctx->max_smem_optin)
-    return fail(PSC_EINVAL, "smoothing tiles do not fit in shared memory");
   {
     std::lock_guard<std::mutex> lk(ctx->scratch_mu);
     const size_t need = sizeof(float) * (size_t)p.n_bins;

@@ -105,6 +105,24 @@ def test_smoothing_conserves_mass_and_delta(small):
     assert np.all(out[..., [0, 1, 3, 4]] == 0)
 
 
+def test_smoothing_of_unaligned_accumulator(small):
+    """A caller-owned accumulator 8 bytes off a 16-byte boundary (through the
+    allocation-free entry point) gives the oracle's result."""
+    torch = small.torch
+    sc = small.sc
+    store = torch.zeros(small.acc.size + 2, dtype=torch.int64, device="cuda")
+    store[1:1 + small.acc.size] = torch.from_numpy(small.acc.ravel()).cuda()
+    acc_t = store[1:1 + small.acc.size]
+    assert acc_t.data_ptr() % 16 == 8
+    sens_t = torch.from_numpy(small.sens_lor.ravel()).cuda()
+    out = torch.full(sc.shape, np.nan, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    psc.psc_finalize_static(acc_t, sc.n_rings, sc.n_crystals, sc.n_rad, sc.n_tof, out, sens=sens_t,
+                            sigma=(2.0, 1.5, 1.0), scale=0.5, stream=stream)
+    exp = oracle.finalize(small.acc, sc.n_rings, sens=small.sens_lor, sigma=(2.0, 1.5, 1.0), scale=0.5)
+    np.testing.assert_allclose(out.cpu().numpy(), exp, rtol=SMOOTH_RTOL, atol=1e-300)
+
+
 def test_finalize_argument_errors(small):
     with pytest.raises(psc.PscError) as e:
         small.run(sigma=(100.0, 1.0, 1.0))
