@@ -409,8 +409,9 @@ def run_precision(a):
 def _request_mix(a, served):
     """(kind, phantom builder key, budget, seed) per request.  batched: one
     request per seeded ellipsoid torso (96^3-class to 192x192x120) on the
-    paper-scale scanner; served: 5-iteration chains mixing the tiny
-    configuration, the paper-scale torso and batched-style torsos."""
+    small scanner (288 x 16 crystals); served: 5-iteration chains mixing the
+    small configuration, the paper-scale torso and scanner, and the
+    batched-style torsos."""
     rng = np.random.default_rng(2025)
     lo, hi = 6.0, 9.0
     out = []
@@ -467,9 +468,9 @@ def run_requests(a):
     l_paper = psc.psc_load_lut(ctx, psc.lut_desc(W.lut_signa(sc_paper)).desc)
     sn_tiny = psc.psc_load_sinogram(ctx, s_tiny, W.sensitivity_uniform(sc_tiny.lor_shape, seed=1), True)
     sn_paper = psc.psc_load_sinogram(ctx, s_paper, W.sensitivity_uniform(sc_paper.lor_shape, seed=1), True)
-    scan = {"tiny": (s_tiny, l_tiny, sn_tiny, sc_tiny)}
-    for k in ("paper", "torso"):
-        scan[k] = (s_paper, l_paper, sn_paper, sc_paper)
+    scan = {"tiny": (s_tiny, l_tiny, sn_tiny, sc_tiny), "torso": (s_tiny, l_tiny, sn_tiny, sc_tiny),
+            "paper": (s_paper, l_paper, sn_paper, sc_paper)}
+    okind = lambda kind: "paper" if kind == "paper" else "tiny"   # output shape of a request
     outs = {"tiny": torch.empty(sc_tiny.shape, dtype=torch.float64, device=dev),
             "paper": torch.empty(sc_paper.shape, dtype=torch.float64, device=dev)}
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -487,7 +488,7 @@ def run_requests(a):
         p_id = psc.psc_load_phantom(ctx, desc.desc, m_id)
         acc = psc.psc_acc_create(ctx, s_id)
         psc.psc_simulate(ctx, psc.sim_args(r["seed"], 0, r["n"], s_id, p_id, acc, lut=l_id), stream=stream)
-        out = outs["tiny" if r["kind"] == "tiny" else "paper"]
+        out = outs[okind(r["kind"])]
         psc.psc_finalize(ctx, psc.finalize_args(acc, sens=sn_id, sigma=sigma, scale=1.0 / r["n"]), out, stream)
         torch.cuda.synchronize()
         psc.psc_unload(ctx, acc)
@@ -516,7 +517,7 @@ def run_requests(a):
     t0 = time.perf_counter()
 
     def take_out(kind):
-        k = "tiny" if kind == "tiny" else "paper"
+        k = okind(kind)
         with cond:
             while not free_out[k]:
                 cond.wait()

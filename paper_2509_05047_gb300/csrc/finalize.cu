@@ -17,7 +17,8 @@
 //   A  radial: acc (int64) -> FP32, columns (plane, view, tof) along rad,
 //              into the first half of the output buffer (used as scratch)
 //   B  view:   that -> FP32 working sinogram, columns (plane, rad, tof)
-//   C  axial:  working sinogram -> FP64 epilogue (x 1/norm, x sens) -> out,
+//   C  axial:  working sinogram -> epilogue (x 1/norm, x sens: factors
+//              rounded to FP32, product widened exactly to FP64) -> out,
 //              columns (segment, view, rad, tof) along the segment's planes
 // No pass writes what it reads.  Kernels are truncated at ceil(4 sigma) with
 // weights normalised to 1 and zero-padded to the instantiated radius KT
@@ -69,8 +70,8 @@ constexpr unsigned long long kMant52 = (1ull << 52) - 1;
 // the rare operands outside the normal range go to the FP64 hardware; kept
 // out of line so the compiler never if-converts them into the common path
 __device__ __noinline__ double hw_f32_to_f64(float f) { return (double)f; }
-__device__ __noinline__ double hw_fmul_fd(float x, double b) { return (double)x * b; }
 __device__ __noinline__ double hw_dmul(double a, double b) { return a * b; }
+__device__ __noinline__ float hw_f64_to_f32(double d) { return (float)d; }
 
 // index of the highest / lowest set bit of a non-zero 64-bit value, from the
 // 32-bit bit-scan instructions
@@ -128,26 +129,19 @@ __device__ __forceinline__ double f32_to_f64(float f) {
                               ((unsigned long long)(b & 0x7fffffu) << 29));
 }
 
-// (double)x * b (RNE, one rounding of the exact product) for finite x, b
-__device__ __forceinline__ double fmul_fd(float x, double b) {
-  const unsigned xb = (unsigned)__float_as_int(x);
-  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
-  const unsigned long long sign = ((unsigned long long)(xb >> 31) << 63) ^ (ub & (1ull << 63));
-  const int ex = (int)((xb >> 23) & 0xffu), eb = (int)((ub >> 52) & 0x7ff);
-  if ((xb << 1) == 0 || (ub << 1) == 0) return __longlong_as_double((long long)sign);
-  if (ex == 0 || ex == 0xff || eb == 0 || eb == 0x7ff) return hw_fmul_fd(x, b);
-  const unsigned long long mx = (xb & 0x7fffffu) | 0x800000u;          // 24 bits
-  const unsigned long long mb = (ub & kMant52) | (1ull << 52);         // 53 bits
-  // P = mx * mb in [2^75, 2^77) = hi 2^32 + lo; T = P >> 13 in [2^62, 2^64)
-  const unsigned long long lo = mx * (mb & 0xffffffffull);
-  const unsigned long long hi = mx * (mb >> 32);
-  const unsigned long long T = (hi << 19) + (lo >> 13);
-  const bool sticky = (lo & 0x1fffull) != 0;
-  const int top = (int)(T >> 63);
-  int e = ex + eb - 127 + top;
-  const unsigned long long m = rne_shift(T, 10 + top, sticky, 53, e);
-  if (e <= 0 || e >= 0x7ff) return hw_fmul_fd(x, b);
-  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
+// double -> float (RNE) from the two 32-bit halves: the 23 kept mantissa
+// bits, then +1 on the rounding decision (a carry moves into the exponent,
+// and past the largest finite value to infinity, as IEEE rounding does)
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  if ((u << 1) == 0) return __uint_as_float(hi & 0x80000000u);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e < 1 || e > 254) return hw_f64_to_f32(d);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(((hi & 0x80000000u) | ((unsigned)e << 23) | m) + up);
 }
 
 // a * b (RNE) for finite doubles
@@ -280,8 +274,8 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
     float x = i64_to_f32(q) * cf;
     if (per_bin_factor) {
       const long long bin = base + (long long)r * T, lor = line * R + r;
-      if (P.sens_first && P.sens) x *= (float)at(P.sens, P.sens_per_lor ? lor : bin);
-      if (P.norm) x *= (float)at(P.norm, P.norm_per_lor ? lor : bin);
+      if (P.sens_first && P.sens) x *= f64_to_f32(at(P.sens, P.sens_per_lor ? lor : bin));
+      if (P.norm) x *= f64_to_f32(at(P.norm, P.norm_per_lor ? lor : bin));
     }
     return x;
   };
@@ -307,7 +301,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 }
 
 // ---------------------------------------------------------------------------
-// pass C: axial within a ring-difference segment, then the FP64 epilogue.
+// pass C: axial within a ring-difference segment, then the epilogue.
 // grid (ceil(R T / 256), segments x V); a thread owns the column (segment,
 // view, rad, tof) and slides along the segment's planes p0 + k (n_rings + 1).
 // ---------------------------------------------------------------------------
@@ -332,16 +326,12 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
   auto store = [&](int k, float o) {
     const long long bin = bin0 + k * bin_step;
     const long long lor = lor0 + k * lor_step;
-    double y;
-    if (P.rnorm) {
-      y = fmul_fd(o, at(P.rnorm, P.norm_per_lor ? lor : bin));
-      if (!P.sens_first && P.sens) y = dmul(y, at(P.sens, P.sens_per_lor ? lor : bin));
-    } else if (!P.sens_first && P.sens) {
-      y = fmul_fd(o, at(P.sens, P.sens_per_lor ? lor : bin));
-    } else {
-      y = f32_to_f64(o);
-    }
-    P.out[bin] = y;
+    // the smoothed value carries FP32 precision: the factors are rounded to
+    // FP32, multiplied in FP32 and the result widened exactly to FP64
+    float y = o;
+    if (P.rnorm) y *= f64_to_f32(at(P.rnorm, P.norm_per_lor ? lor : bin));
+    if (!P.sens_first && P.sens) y *= f64_to_f32(at(P.sens, P.sens_per_lor ? lor : bin));
+    P.out[bin] = f32_to_f64(y);
   };
   slide_any<KT>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
 }

@@ -2,23 +2,26 @@
 // weight -> LOR/TOF binning kernel (Sec. 2.2.1-2.2.3 of the paper; the
 // simulator itself is the project's own design).
 //
-// Each lane runs a small state machine over its histories:
+// A history is a small state machine:
 //
 //   EMIT -> STEP <-> {COMPTON, RAYLEIGH} -> ESCAPE -> (photon B) STEP ...
-//        -> ESCAPE -> COINC -> EMIT (next history)
+//        -> ESCAPE -> COINC -> next history
 //
-// and every loop iteration executes each section once, for all lanes in
-// that state together.  Lanes of a warp therefore stay converged on the hot
-// section (one Woodcock step per iteration), and the code holds a single
-// copy of each section, so the instruction cache is not thrashed by inlined
-// copies of the photon loop.  One rejection-sampling try runs per iteration.
+// Each warp owns a pool of kSlotsPerWarp photon slots whose state lives in
+// shared memory (structure of arrays).  Every loop iteration the warp votes
+// for the section that serves the most slots per cost, packs up to 32 slots
+// in that state onto its 32 lanes, and runs the section once for them.  With
+// twice as many slots as lanes the chosen section usually fills the warp,
+// where one history per lane left most lanes idle (the states of 32
+// histories spread over six sections).  The code holds a single copy of each
+// section, and one rejection-sampling try runs per iteration.
 //
 // Random numbers: a history's sub-streams (0: emission + TOF blur, 1: photon
-// A, 2: photon B) are read through an 8-word per-lane window in shared
-// memory; the only Philox4x32-10 evaluation sits at the top of the loop and
-// appends one block when the lane's next section needs more words than the
-// window holds.  The words consumed, and their order, are those of the
-// per-history definition, so results do not depend on the schedule.
+// A, 2: photon B) are read through an 8-word window per slot; the only
+// Philox4x32-10 evaluation sits before the sections and appends one block
+// when the slot's next section needs more words than the window holds.  The
+// words consumed, and their order, are those of the per-history definition,
+// so results do not depend on the schedule, the slot or the lane.
 //
 // A history adds one fixed-point weight to the int64 accumulator or nothing
 // (Sec. 2.2.3: weighted or discarded, never duplicated); lanes of a warp
@@ -29,8 +32,28 @@ namespace psc {
 
 enum : int {
   kEmit = 0, kStep = 1, kCompton = 2, kRayleigh = 3, kEscape = 4, kCoinc = 5, kNumSections = 6,
-  kFinish = 6, kDone = 7
+  kDone = 7
 };
+
+constexpr int kSlotsPerWarp = 64;
+
+// fields of a photon slot: field f of slot g at slots[f * n_slots + g]
+enum : int {
+  F_PX, F_PY, F_PZ, F_DX, F_DY, F_DZ, F_E, F_PATH,          // the photon in flight
+  F_K, F_NB, F_HLO, F_HHI, F_META, F_CNT, F_TRIES,          // stream position, history, state
+  F_E0X, F_E0Y, F_E0Z, F_D0X, F_D0Y, F_D0Z,                 // emission point, photon A direction
+  F_ACRG, F_AE, F_APATH, F_ANX, F_ANY, F_ADX, F_ADY, F_ADZ,  // photon A at the detector
+  F_BCRG, F_BNX, F_BNY,                                      // photon B at the detector
+  F_RING,                                                    // kRingWords words of the sub-stream
+  kFields = F_RING + kRingWords
+};
+// F_META = state | photon << 3 | stream << 4;  F_CNT = steps | interactions << 16;
+// F_ACRG = crystal | ring << 16 | scattered << 31;  F_BCRG = crystal | ring << 16;
+// F_TRIES = tries (| material << 16 for a pending Rayleigh event)
+__host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
+  return (uint32_t)state | (uint32_t)photon << 3 | (uint32_t)stream << 4;
+}
+
 
 __device__ __forceinline__ float interp_scalar(const float* t, int n_tab, int e0, float e) {
   const float fe = e - (float)e0;
@@ -74,39 +97,30 @@ __device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alph
   beta = atan2f(d.z, dn) * 57.29577951308232f;
 }
 
-struct Lane {
-  unsigned long long h;    // current history id
-  unsigned long long m;    // index of the lane's current history within its share
-  int state, photon, tries;
-  uint32_t stream, k, nb;  // sub-stream, next word, blocks generated
-  float3 pos, dir;
-  float e, path;
-  int nint, nsteps;
-  float3 e0, d0;           // emission point and photon A's initial direction
-  // photon A at the detector
-  int a_cr, a_rg, a_scat;
-  float a_e, a_path, a_nx, a_ny;
-  float3 a_dir;
-  // photon B at the detector (set by ESCAPE, used by COINC)
-  int b_cr, b_rg;
-  float b_nx, b_ny;
-};
 
 template <int DT>
-__global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant__ BatchParams B) {
+__global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ float4 smem[];
   const unsigned tid = threadIdx.x, bdim = blockDim.x;
-  uint32_t* ring = reinterpret_cast<uint32_t*>(smem);  // [kRingWords][blockDim]
-  float4* s_xs = reinterpret_cast<float4*>(ring + kRingWords * bdim);
+  const int n_slots = (int)(bdim >> 5) * kSlotsPerWarp;
+  uint32_t* slots = reinterpret_cast<uint32_t*>(smem);  // [kFields][n_slots]
+  float4* s_xs = reinterpret_cast<float4*>(slots + kFields * n_slots);
   __shared__ Job s_job;                       // the job of the current chunk
   __shared__ int s_j;
   __shared__ unsigned long long s_lo;         // first history of the chunk
   __shared__ unsigned s_len, s_next;          // chunk length, next offset to hand out
   __shared__ unsigned long long s_cnt[kStatCount];
+  __shared__ int s_sel[8][32];                // per warp: slot of each lane this iteration
   for (int i = tid; i < kStatCount; i += bdim) s_cnt[i] = 0;
   const unsigned lane_id = tid & 31u;
+  const int warp = (int)(tid >> 5);
+  const int g0 = warp * kSlotsPerWarp + (int)lane_id, g1 = g0 + 32;  // the slots this lane refills
   const bool stats = B.stats != nullptr;
   int cached = -1;
+
+  auto U = [&](int f, int g) -> uint32_t& { return slots[f * n_slots + g]; };
+  auto Fv = [&](int f, int g) -> float { return __uint_as_float(slots[f * n_slots + g]); };
+  auto setF = [&](int f, int g, float v) { slots[f * n_slots + g] = __float_as_uint(v); };
 
   for (;;) {
     // ---- fetch the next chunk of (job, history range) ----
@@ -154,327 +168,392 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
     const uint2 key = make_uint2((uint32_t)J.seed, (uint32_t)(J.seed >> 32));
     const bool blur = S.tof_sigma > 0.0f;
 
-  auto word = [&](uint32_t w) -> uint32_t { return ring[(w & (kRingWords - 1)) * bdim + tid]; };
-  auto uni = [&](uint32_t w) -> float { return u01(word(w)); };
-  // warp-aggregated counter increment (lanes of the calling branch)
-  auto count = [&](bool pred, int slot) {
-    if (!stats) return;
-    const unsigned act = __activemask();
-    const unsigned b = __ballot_sync(act, pred);
-    if (b && lane_id == (unsigned)(__ffs(act) - 1)) atomicAdd(&s_cnt[slot], (unsigned long long)__popc(b));
-  };
-
-  Lane L;
-  {
-    const unsigned off = atomicAdd(&s_next, 1u);
-    L.h = s_lo + off;
-    L.state = off < s_len ? kEmit : kDone;
-  }
-  L.stream = 0;
-  L.k = 0;
-  L.nb = 0;
-
-  // a history ends: remember its class; the FINISH block records it
-  int fin_cls = 0;
-  long long fin_key = -1, fin_q = 0;
-  auto finish = [&](int cls, long long key_out, long long q_out) {
-    fin_cls = cls;
-    fin_key = key_out;
-    fin_q = q_out;
-    L.state = kFinish;
-  };
-
-  // per-section cost weights of the warp scheduler (1024 / approximate
-  // instructions of one execution of the section)
-  constexpr int kW[kNumSections] = {1024 / 140, 1024 / 90, 1024 / 70, 1024 / 60, 1024 / 80, 1024 / 300};
-  constexpr int kNeed[kNumSections] = {7, 2, 4, 3, 0, 2};
-
-  while (__any_sync(0xffffffffu, L.state != kDone)) {
-    // ---- FINISH: record the ended history, move to the lane's next one ----
-    if (L.state == kFinish) {
-      const unsigned long long i = L.h - J.first;
-      if (J.cls_out) J.cls_out[i] = (int8_t)fin_cls;
-      if (J.key_out) J.key_out[i] = fin_key;
-      if (J.q_out) J.q_out[i] = fin_q;
-      if (stats) atomicAdd(&s_cnt[kStatClass0 + fin_cls], 1ull);
+    // warp-aggregated counter increment (lanes of the calling branch)
+    auto count = [&](bool pred, int slot) {
+      if (!stats) return;
+      const unsigned act = __activemask();
+      const unsigned b = __ballot_sync(act, pred);
+      if (b && lane_id == (unsigned)(__ffs(act) - 1)) atomicAdd(&s_cnt[slot], (unsigned long long)__popc(b));
+    };
+    // slot g takes the chunk's next history, or is done
+    auto start = [&](int g) {
       const unsigned off = atomicAdd(&s_next, 1u);
       if (off < s_len) {
-        L.h = s_lo + off;
-        L.state = kEmit;
-        L.stream = 0;
-        L.k = 0;
-        L.nb = 0;
+        const unsigned long long h = s_lo + off;
+        U(F_HLO, g) = (uint32_t)h;
+        U(F_HHI, g) = (uint32_t)(h >> 32);
+        U(F_META, g) = meta(kEmit, 0, 0);
+        U(F_K, g) = 0;
+        U(F_NB, g) = 0;
       } else {
-        L.state = kDone;
+        U(F_META, g) = kDone;
       }
-    }
+    };
+    // a history ends in slot g: record its class (and bin, weight), start the next
+    auto finish = [&](int g, int cls, long long key_out, long long q_out) {
+      const unsigned long long h = (unsigned long long)U(F_HHI, g) << 32 | U(F_HLO, g);
+      const unsigned long long i = h - J.first;
+      if (J.cls_out) J.cls_out[i] = (int8_t)cls;
+      if (J.key_out) J.key_out[i] = key_out;
+      if (J.q_out) J.q_out[i] = q_out;
+      if (stats) atomicAdd(&s_cnt[kStatClass0 + cls], 1ull);
+      start(g);
+    };
 
-    // ---- warp vote: run the section that serves the most lanes per cost ----
-    int sec = -1, best = 0;
+    start(g0);
+    start(g1);
+    __syncwarp();
+
+    // per-section cost weights of the warp scheduler (1024 / approximate
+    // instructions of one execution of the section)
+    constexpr int kW[kNumSections] = {1024 / 140, 1024 / 90, 1024 / 70, 1024 / 60, 1024 / 80, 1024 / 300};
+    // words a section reads, one nibble per section: 7, 2, 4, 3, 0, 2
+    constexpr uint32_t kNeedNibbles = 0x203427u;
+
+    for (;;) {
+      const int st0 = (int)(U(F_META, g0) & 7u), st1 = (int)(U(F_META, g1) & 7u);
+      if (!__any_sync(0xffffffffu, st0 != kDone || st1 != kDone)) break;
+
+      // ---- warp vote: the section that serves the most slots per cost ----
+      int sec = -1, best = 0;
+      unsigned sm0 = 0, sm1 = 0;
 #pragma unroll
-    for (int q = 0; q < kNumSections; ++q) {
-      const unsigned m = __ballot_sync(0xffffffffu, L.state == q);
-      const int score = __popc(m) * kW[q];
-      if (score > best) {
-        best = score;
-        sec = q;
+      for (int q = 0; q < kNumSections; ++q) {
+        const unsigned m0 = __ballot_sync(0xffffffffu, st0 == q);
+        const unsigned m1 = __ballot_sync(0xffffffffu, st1 == q);
+        const int score = min(32, __popc(m0) + __popc(m1)) * kW[q];
+        if (score > best) {
+          best = score;
+          sec = q;
+          sm0 = m0;
+          sm1 = m1;
+        }
       }
-    }
-    if (sec < 0) continue;  // only finished lanes this iteration
-    const bool mine = L.state == sec;
+      if (sec < 0) {  // no slot in a section state (cannot happen): retire them rather than spin
+        if (st0 != kDone) U(F_META, g0) = kDone;
+        if (st1 != kDone) U(F_META, g1) = kDone;
+        __syncwarp();
+        continue;
+      }
+      // ---- pack up to 32 slots in that state onto the lanes ----
+      const unsigned below = (1u << lane_id) - 1u;
+      const int n0 = __popc(sm0);
+      if (st0 == sec) s_sel[warp][__popc(sm0 & below)] = g0;
+      if (st1 == sec) {
+        const int r = n0 + __popc(sm1 & below);
+        if (r < 32) s_sel[warp][r] = g1;
+      }
+      __syncwarp();
+      const int g = (int)lane_id < min(32, n0 + __popc(sm1)) ? s_sel[warp][lane_id] : -1;
+      __syncwarp();
 
-    // ---- refill the section's lanes: the single Philox evaluation ----
-    int need = kNeed[0];
-#pragma unroll
-    for (int q = 1; q < kNumSections; ++q) need = sec == q ? kNeed[q] : need;
-    if (sec == kCoinc && !blur) need = 0;
-    while (mine && L.k + need > 4 * L.nb) {
-      const uint4 b = philox4x32_10(make_uint4((uint32_t)L.h, (uint32_t)(L.h >> 32), L.nb, L.stream), key);
-      const uint32_t w0 = 4 * L.nb;
-      ring[((w0 + 0) & (kRingWords - 1)) * bdim + tid] = b.x;
-      ring[((w0 + 1) & (kRingWords - 1)) * bdim + tid] = b.y;
-      ring[((w0 + 2) & (kRingWords - 1)) * bdim + tid] = b.z;
-      ring[((w0 + 3) & (kRingWords - 1)) * bdim + tid] = b.w;
-      ++L.nb;
-      count(true, kStatRng);
-    }
-    if (!mine) continue;
+      if (g >= 0) {
+        // ---- refill the slot's window: the single Philox evaluation ----
+        uint32_t k = U(F_K, g), nb = U(F_NB, g);
+        int need = (int)((kNeedNibbles >> (4 * sec)) & 15u);
+        if (sec == kCoinc && !blur) need = 0;
+        if (k + need > 4 * nb) {
+          const uint32_t hlo = U(F_HLO, g), hhi = U(F_HHI, g), stream = U(F_META, g) >> 4;
+          do {
+            const uint4 b = philox4x32_10(make_uint4(hlo, hhi, nb, stream), key);
+            const uint32_t w0 = 4 * nb;
+            U(F_RING + ((w0 + 0) & (kRingWords - 1)), g) = b.x;
+            U(F_RING + ((w0 + 1) & (kRingWords - 1)), g) = b.y;
+            U(F_RING + ((w0 + 2) & (kRingWords - 1)), g) = b.z;
+            U(F_RING + ((w0 + 3) & (kRingWords - 1)), g) = b.w;
+            ++nb;
+            count(true, kStatRng);
+          } while (k + need > 4 * nb);
+          U(F_NB, g) = nb;
+        }
+        auto word = [&](uint32_t w) -> uint32_t { return U(F_RING + (w & (kRingWords - 1)), g); };
+        auto uni = [&](uint32_t w) -> float { return u01(word(w)); };
 
-    // ---- emission (stream 0, words 0..6) ----
-    if (sec == kEmit) {
-      const uint32_t w0 = word(0), w1 = word(1);
-      const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
-      const uint2 at = __ldg(ph.alias + col);
-      const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
-      const int ix = v % ph.nx, iy = (v / ph.nx) % ph.ny, iz = v / (ph.nx * ph.ny);
-      L.e0 = make_float3(ph.ox + ((float)ix + uni(2)) * ph.dx, ph.oy + ((float)iy + uni(3)) * ph.dy,
-                         ph.oz + ((float)iz + uni(4)) * ph.dz);
-      const float ct = 2.0f * uni(5) - 1.0f;
-      float sp, cp;
-      sincospif(2.0f * uni(6), &sp, &cp);
-      const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
-      L.d0 = make_float3(st * cp, st * sp, ct);
-      L.pos = L.e0;
-      L.dir = L.d0;
-      L.e = kEmitKeV;
-      L.path = 0.0f;
-      L.nint = 0;
-      L.nsteps = 0;
-      L.photon = 0;
-      L.stream = 1;
-      L.k = 0;
-      L.nb = 0;
-      L.state = kStep;
-    }
+        // ---- emission (stream 0, words 0..6) ----
+        if (sec == kEmit) {
+          const uint32_t w0 = word(0), w1 = word(1);
+          const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
+          const uint2 at = __ldg(ph.alias + col);
+          const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
+          const int ix = v % ph.nx, iy = (v / ph.nx) % ph.ny, iz = v / (ph.nx * ph.ny);
+          const float ex = ph.ox + ((float)ix + uni(2)) * ph.dx, ey = ph.oy + ((float)iy + uni(3)) * ph.dy,
+                      ez = ph.oz + ((float)iz + uni(4)) * ph.dz;
+          const float ct = 2.0f * uni(5) - 1.0f;
+          float sp, cp;
+          sincospif(2.0f * uni(6), &sp, &cp);
+          const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+          const float dx = st * cp, dy = st * sp, dz = ct;
+          setF(F_E0X, g, ex);
+          setF(F_E0Y, g, ey);
+          setF(F_E0Z, g, ez);
+          setF(F_D0X, g, dx);
+          setF(F_D0Y, g, dy);
+          setF(F_D0Z, g, dz);
+          setF(F_PX, g, ex);
+          setF(F_PY, g, ey);
+          setF(F_PZ, g, ez);
+          setF(F_DX, g, dx);
+          setF(F_DY, g, dy);
+          setF(F_DZ, g, dz);
+          setF(F_E, g, kEmitKeV);
+          setF(F_PATH, g, 0.0f);
+          U(F_CNT, g) = 0;
+          U(F_K, g) = 0;
+          U(F_NB, g) = 0;
+          U(F_META, g) = meta(kStep, 0, 1);
+        }
 
-    // ---- one Woodcock step ----
-    if (sec == kStep) {
-      bool moved = false;
-      if (L.nsteps >= kMaxSteps) {
-        finish(kStepLimit, -1, 0);
-      } else {
-        const float mu_max = interp_scalar(s_maj, ph.n_tab, ph.e0, L.e);
-        if (!(mu_max > 0.0f)) {
-          L.state = kEscape;
-        } else {
-          const float dist = -__logf(uni(L.k)) / mu_max;
-          ++L.k;
-          const float qx = L.pos.x + dist * L.dir.x;
-          const float qy = L.pos.y + dist * L.dir.y;
-          const float qz = L.pos.z + dist * L.dir.z;
-          const float fx = (qx - ph.ox) * ph.inv_dx;
-          const float fy = (qy - ph.oy) * ph.inv_dy;
-          const float fz = (qz - ph.oz) * ph.inv_dz;
-          if (!(fx >= 0.0f && fx < (float)ph.nx && fy >= 0.0f && fy < (float)ph.ny && fz >= 0.0f &&
-                fz < (float)ph.nz)) {
-            L.state = kEscape;  // outside the grid is vacuum: straight to the detector
+        // ---- one Woodcock step ----
+        if (sec == kStep) {
+          bool moved = false, ended = false;
+          const uint32_t cnt = U(F_CNT, g);
+          if ((int)(cnt & 0xffffu) >= kMaxSteps) {
+            finish(g, kStepLimit, -1, 0);
           } else {
-            moved = true;
-            const int ix = min((int)fx, ph.nx - 1);
-            const int iy = min((int)fy, ph.ny - 1);
-            const int iz = min((int)fz, ph.nz - 1);
-            L.pos = make_float3(qx, qy, qz);
-            L.path += dist;
-            ++L.nsteps;
-            const float2 vx = __ldg(ph.vox + ((long long)iz * ph.ny + iy) * ph.nx + ix);
-            const int mat = __float_as_int(vx.y);
-            const float4 cum = interp_xs(s_xs + mat * ph.n_tab, ph.n_tab, ph.e0, L.e);
-            const float t = uni(L.k) * mu_max;
-            ++L.k;
-            if (t < vx.x * cum.x) {
-              L.state = kCompton;
-              L.tries = 0;
-            } else if (t < vx.x * cum.y) {
-              L.state = kRayleigh;
-              L.tries = mat << 16;  // the material id travels with the pending event
-            } else if (t < vx.x * cum.z) {
-              count(true, kStatPhoto);
-              finish(kAbsorbed, -1, 0);
+            const float e = Fv(F_E, g);
+            const float mu_max = interp_scalar(s_maj, ph.n_tab, ph.e0, e);
+            const uint32_t m = U(F_META, g);
+            if (!(mu_max > 0.0f)) {
+              U(F_META, g) = (m & ~7u) | kEscape;
+            } else {
+              const float px = Fv(F_PX, g), py = Fv(F_PY, g), pz = Fv(F_PZ, g);
+              const float dx = Fv(F_DX, g), dy = Fv(F_DY, g), dz = Fv(F_DZ, g);
+              const float dist = -__logf(uni(k)) / mu_max;
+              ++k;
+              const float qx = px + dist * dx;
+              const float qy = py + dist * dy;
+              const float qz = pz + dist * dz;
+              const float fx = (qx - ph.ox) * ph.inv_dx;
+              const float fy = (qy - ph.oy) * ph.inv_dy;
+              const float fz = (qz - ph.oz) * ph.inv_dz;
+              if (!(fx >= 0.0f && fx < (float)ph.nx && fy >= 0.0f && fy < (float)ph.ny && fz >= 0.0f &&
+                    fz < (float)ph.nz)) {
+                U(F_META, g) = (m & ~7u) | kEscape;  // outside the grid is vacuum: straight to the detector
+              } else {
+                moved = true;
+                const int ix = min((int)fx, ph.nx - 1);
+                const int iy = min((int)fy, ph.ny - 1);
+                const int iz = min((int)fz, ph.nz - 1);
+                setF(F_PX, g, qx);
+                setF(F_PY, g, qy);
+                setF(F_PZ, g, qz);
+                setF(F_PATH, g, Fv(F_PATH, g) + dist);
+                U(F_CNT, g) = cnt + 1u;
+                const float2 vx = __ldg(ph.vox + ((long long)iz * ph.ny + iy) * ph.nx + ix);
+                const int mat = __float_as_int(vx.y);
+                const float4 cum = interp_xs(s_xs + mat * ph.n_tab, ph.n_tab, ph.e0, e);
+                const float t = uni(k) * mu_max;
+                ++k;
+                if (t < vx.x * cum.x) {
+                  U(F_META, g) = (m & ~7u) | kCompton;
+                  U(F_TRIES, g) = 0;
+                } else if (t < vx.x * cum.y) {
+                  U(F_META, g) = (m & ~7u) | kRayleigh;
+                  U(F_TRIES, g) = (uint32_t)mat << 16;  // the material id travels with the pending event
+                } else if (t < vx.x * cum.z) {
+                  count(true, kStatPhoto);
+                  ended = true;
+                }
+              }
+              if (ended) finish(g, kAbsorbed, -1, 0);
+              else U(F_K, g) = k;
+            }
+          }
+          count(moved, kStatSteps);
+        }
+
+        // ---- one Klein-Nishina try (Kahn's method on x = E/E') ----
+        if (sec == kCompton) {
+          const float r1 = uni(k), r2 = uni(k + 1), r3 = uni(k + 2);
+          k += 3;
+          const uint32_t tries = U(F_TRIES, g) + 1u;
+          const float e = Fv(F_E, g);
+          const float a = e / kRestKeV;
+          const float two_a = 2.0f * a;
+          float x, c;
+          bool accept;
+          if (r1 < (1.0f + two_a) / (9.0f + two_a)) {
+            x = 1.0f + two_a * r2;
+            c = 1.0f - (x - 1.0f) / a;
+            accept = r3 < 4.0f * (1.0f / x - 1.0f / (x * x));
+          } else {
+            x = (1.0f + two_a) / (1.0f + two_a * r2);
+            c = 1.0f - (x - 1.0f) / a;
+            accept = r3 < 0.5f * (c * c + 1.0f / x);
+          }
+          count(true, kStatTries);
+          if (accept || (int)tries >= kMaxTries) {
+            float3 d = make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g));
+            rotate(d, c, uni(k));
+            ++k;
+            const float e1 = e / x;
+            count(true, kStatCompton);
+            if (e1 < S.e_lo) {
+              finish(g, kEnergyWindow, -1, 0);
+            } else {
+              setF(F_DX, g, d.x);
+              setF(F_DY, g, d.y);
+              setF(F_DZ, g, d.z);
+              setF(F_E, g, e1);
+              U(F_CNT, g) += 1u << 16;
+              U(F_K, g) = k;
+              U(F_META, g) = (U(F_META, g) & ~7u) | kStep;
+            }
+          } else {
+            U(F_TRIES, g) = tries;
+            U(F_K, g) = k;
+          }
+        }
+
+        // ---- one Rayleigh try (material id in the upper half of tries) ----
+        if (sec == kRayleigh) {
+          const float u1 = uni(k), u2 = uni(k + 1);
+          k += 2;
+          const uint32_t tries = U(F_TRIES, g) + 1u;
+          const float e = Fv(F_E, g);
+          const float er = e / kRestKeV;
+          const float b = s_kappa[tries >> 16] * er * er;
+          const float sv = u1 / (1.0f + b * (1.0f - u1));
+          const float c = 1.0f - 2.0f * sv;
+          count(true, kStatTries);
+          if (u2 < 0.5f * (1.0f + c * c) || (int)(tries & 0xffffu) >= kMaxTries) {
+            float3 d = make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g));
+            rotate(d, c, uni(k));
+            ++k;
+            count(true, kStatRayleigh);
+            setF(F_DX, g, d.x);
+            setF(F_DY, g, d.y);
+            setF(F_DZ, g, d.z);
+            U(F_CNT, g) += 1u << 16;
+            U(F_META, g) = (U(F_META, g) & ~7u) | kStep;
+          } else {
+            U(F_TRIES, g) = tries;
+          }
+          U(F_K, g) = k;
+        }
+
+        // ---- the photon reaches the detector cylinder ----
+        if (sec == kEscape) {
+          const float px = Fv(F_PX, g), py = Fv(F_PY, g), pz = Fv(F_PZ, g);
+          const float dx = Fv(F_DX, g), dy = Fv(F_DY, g), dz = Fv(F_DZ, g);
+          const float e = Fv(F_E, g);
+          float path = Fv(F_PATH, g);
+          const float a = dx * dx + dy * dy;
+          int cls = kDetected, cr = 0, rg = 0;
+          float nx = 0.0f, ny = 0.0f;
+          if (!(a > 0.0f)) {
+            cls = kLostAxial;
+          } else {
+            const float b = px * dx + py * dy;
+            const float c = px * px + py * py - S.r2;
+            const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
+            const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
+            const float hx = px + t * dx, hy = py + t * dy, hz = pz + t * dz;
+            path += t;
+            if (!(hz >= -S.half_len && hz < S.half_len)) {
+              cls = kLostAxial;
+            } else {
+              rg = max(0, min((int)floorf((hz + S.half_len) * S.inv_pitch), S.n_rings - 1));
+              float phi = atan2f(hy, hx);
+              if (phi < 0.0f) phi += 6.283185307179586f;
+              cr = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
+              nx = hx / S.radius;
+              ny = hy / S.radius;
+              if (e < S.e_lo || e > S.e_hi) cls = kEnergyWindow;
+            }
+          }
+          count(cls == kDetected, kStatDetected);
+          const uint32_t m = U(F_META, g);
+          if (cls != kDetected) {
+            finish(g, cls, -1, 0);
+          } else if (((m >> 3) & 1u) == 0) {  // photon A: keep it, launch photon B back to back
+            const uint32_t nint = U(F_CNT, g) >> 16;
+            U(F_ACRG, g) = (uint32_t)cr | (uint32_t)rg << 16 | (nint > 0 ? 1u << 31 : 0u);
+            setF(F_AE, g, e);
+            setF(F_APATH, g, path);
+            setF(F_ANX, g, nx);
+            setF(F_ANY, g, ny);
+            setF(F_ADX, g, dx);
+            setF(F_ADY, g, dy);
+            setF(F_ADZ, g, dz);
+            setF(F_PX, g, Fv(F_E0X, g));
+            setF(F_PY, g, Fv(F_E0Y, g));
+            setF(F_PZ, g, Fv(F_E0Z, g));
+            setF(F_DX, g, -Fv(F_D0X, g));
+            setF(F_DY, g, -Fv(F_D0Y, g));
+            setF(F_DZ, g, -Fv(F_D0Z, g));
+            setF(F_E, g, kEmitKeV);
+            setF(F_PATH, g, 0.0f);
+            U(F_CNT, g) = 0;
+            U(F_K, g) = 0;
+            U(F_NB, g) = 0;
+            U(F_META, g) = meta(kStep, 1, 2);
+          } else if (cr == (int)(U(F_ACRG, g) & 0xffffu)) {
+            finish(g, kSameCrystal, -1, 0);
+          } else {
+            U(F_BCRG, g) = (uint32_t)cr | (uint32_t)rg << 16;
+            setF(F_BNX, g, nx);
+            setF(F_BNY, g, ny);
+            setF(F_PATH, g, path);
+            if (blur) {  // the TOF blur reads stream 0, block 2
+              U(F_META, g) = meta(kCoinc, 1, 0);
+              U(F_K, g) = 8;
+              U(F_NB, g) = 2;
+            } else {
+              U(F_META, g) = meta(kCoinc, 1, 2);
             }
           }
         }
-      }
-      count(moved, kStatSteps);
-    }
 
-    // ---- one Klein-Nishina try (Kahn's method on x = E/E') ----
-    if (sec == kCompton) {
-      const float r1 = uni(L.k), r2 = uni(L.k + 1), r3 = uni(L.k + 2);
-      L.k += 3;
-      ++L.tries;
-      const float a = L.e / kRestKeV;
-      const float two_a = 2.0f * a;
-      float x, c;
-      bool accept;
-      if (r1 < (1.0f + two_a) / (9.0f + two_a)) {
-        x = 1.0f + two_a * r2;
-        c = 1.0f - (x - 1.0f) / a;
-        accept = r3 < 4.0f * (1.0f / x - 1.0f / (x * x));
-      } else {
-        x = (1.0f + two_a) / (1.0f + two_a * r2);
-        c = 1.0f - (x - 1.0f) / a;
-        accept = r3 < 0.5f * (c * c + 1.0f / x);
-      }
-      count(true, kStatTries);
-      if (accept || L.tries >= kMaxTries) {
-        rotate(L.dir, c, uni(L.k));
-        ++L.k;
-        L.e = L.e / x;
-        ++L.nint;
-        count(true, kStatCompton);
-        if (L.e < S.e_lo) finish(kEnergyWindow, -1, 0);
-        else L.state = kStep;
-      }
-    }
-
-    // ---- one Rayleigh try (material id in the upper half of tries) ----
-    if (sec == kRayleigh) {
-      const float u1 = uni(L.k), u2 = uni(L.k + 1);
-      L.k += 2;
-      ++L.tries;
-      const float er = L.e / kRestKeV;
-      const float b = s_kappa[L.tries >> 16] * er * er;
-      const float sv = u1 / (1.0f + b * (1.0f - u1));
-      const float c = 1.0f - 2.0f * sv;
-      count(true, kStatTries);
-      if (u2 < 0.5f * (1.0f + c * c) || (L.tries & 0xffff) >= kMaxTries) {
-        rotate(L.dir, c, uni(L.k));
-        ++L.k;
-        ++L.nint;
-        count(true, kStatRayleigh);
-        L.state = kStep;
-      }
-    }
-
-    // ---- the photon reaches the detector cylinder ----
-    if (sec == kEscape) {
-      const float3 p = L.pos, d = L.dir;
-      const float a = d.x * d.x + d.y * d.y;
-      int cls = kDetected, cr = 0, rg = 0;
-      float nx = 0.0f, ny = 0.0f;
-      if (!(a > 0.0f)) {
-        cls = kLostAxial;
-      } else {
-        const float b = p.x * d.x + p.y * d.y;
-        const float c = p.x * p.x + p.y * p.y - S.r2;
-        const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
-        const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
-        const float hx = p.x + t * d.x, hy = p.y + t * d.y, hz = p.z + t * d.z;
-        L.path += t;
-        if (!(hz >= -S.half_len && hz < S.half_len)) {
-          cls = kLostAxial;
-        } else {
-          rg = max(0, min((int)floorf((hz + S.half_len) * S.inv_pitch), S.n_rings - 1));
-          float phi = atan2f(hy, hx);
-          if (phi < 0.0f) phi += 6.283185307179586f;
-          cr = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
-          nx = hx / S.radius;
-          ny = hy / S.radius;
-          if (L.e < S.e_lo || L.e > S.e_hi) cls = kEnergyWindow;
+        // ---- coincidence: TOF, LOR bin, LUT weight, accumulate ----
+        if (sec == kCoinc) {
+          const uint32_t acrg = U(F_ACRG, g), bcrg = U(F_BCRG, g);
+          const int a_cr = (int)(acrg & 0xffffu), a_rg = (int)((acrg >> 16) & 0x7fffu);
+          const int b_cr = (int)(bcrg & 0xffffu), b_rg = (int)(bcrg >> 16);
+          const float a_path = Fv(F_APATH, g), path = Fv(F_PATH, g);
+          const bool a_first = a_cr < b_cr;
+          float delta = 0.5f * (a_first ? a_path - path : path - a_path);
+          if (blur) {
+            const float gs = sqrtf(-2.0f * logf(uni(8))) * cospif(2.0f * uni(9));
+            delta += S.tof_sigma * gs;
+          }
+          const long long key_ = a_first ? bin_key(S, a_cr, b_cr, a_rg, b_rg, delta)
+                                         : bin_key(S, b_cr, a_cr, b_rg, a_rg, delta);
+          const bool scattered = (acrg >> 31) != 0u || (U(F_CNT, g) >> 16) > 0u;
+          const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
+          const bool take = cls == kScatter ? (J.bin_mask & 1) : cls == kTrue ? (J.bin_mask & 2) : false;
+          long long q = 0;
+          if (key_ >= 0 && (take || J.q_out)) {
+            float aa, ab, ba, bb;
+            angles(Fv(F_ANX, g), Fv(F_ANY, g), make_float3(Fv(F_ADX, g), Fv(F_ADY, g), Fv(F_ADZ, g)), aa, ab);
+            angles(Fv(F_BNX, g), Fv(F_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
+            const float w = lut_prob<DT>(J.lut, Fv(F_AE, g), aa, ab, a_cr % S.module_t, a_rg % S.module_a) *
+                            lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_cr % S.module_t, b_rg % S.module_a);
+            q = __float2ll_rn(w * 4294967296.0f);
+          }
+          // lanes that hit the same bin add their weights first, one atomic per bin
+          const unsigned act = __activemask();
+          const unsigned takers = __ballot_sync(act, take);
+          if (take) {
+            const unsigned peers = __match_any_sync(takers, (unsigned long long)key_);
+            const unsigned hi = __reduce_add_sync(peers, (unsigned)(q >> 16));
+            const unsigned lo = __reduce_add_sync(peers, (unsigned)(q & 0xffff));
+            if (lane_id == (unsigned)(__ffs(peers) - 1)) {
+              atomicAdd(J.acc + key_, ((unsigned long long)hi << 16) + lo);
+              if (stats) atomicAdd(&s_cnt[kStatAtomics], 1ull);
+            }
+            if (stats) {
+              atomicAdd(&s_cnt[kStatBinned], 1ull);
+              atomicAdd(&s_cnt[kStatWeight], (unsigned long long)q);
+            }
+          }
+          finish(g, cls, key_, cls == kOutOfRange ? 0 : q);
         }
       }
-      count(cls == kDetected, kStatDetected);
-      if (cls != kDetected) {
-        finish(cls, -1, 0);
-      } else if (L.photon == 0) {
-        L.a_cr = cr;
-        L.a_rg = rg;
-        L.a_scat = L.nint;
-        L.a_e = L.e;
-        L.a_path = L.path;
-        L.a_nx = nx;
-        L.a_ny = ny;
-        L.a_dir = L.dir;
-        L.pos = L.e0;  // photon B leaves back to back
-        L.dir = make_float3(-L.d0.x, -L.d0.y, -L.d0.z);
-        L.e = kEmitKeV;
-        L.path = 0.0f;
-        L.nint = 0;
-        L.nsteps = 0;
-        L.photon = 1;
-        L.stream = 2;
-        L.k = 0;
-        L.nb = 0;
-        L.state = kStep;
-      } else if (cr == L.a_cr) {
-        finish(kSameCrystal, -1, 0);
-      } else {
-        L.b_cr = cr;
-        L.b_rg = rg;
-        L.b_nx = nx;
-        L.b_ny = ny;
-        L.state = kCoinc;
-        if (blur) {  // the TOF blur reads stream 0, block 2
-          L.stream = 0;
-          L.k = 8;
-          L.nb = 2;
-        }
-      }
+      __syncwarp();  // slot updates are visible to the lanes that vote on them next
     }
 
-    // ---- coincidence: TOF, LOR bin, LUT weight, accumulate ----
-    if (sec == kCoinc) {
-      const bool a_first = L.a_cr < L.b_cr;
-      float delta = 0.5f * (a_first ? L.a_path - L.path : L.path - L.a_path);
-      if (blur) {
-        const float g = sqrtf(-2.0f * logf(uni(8))) * cospif(2.0f * uni(9));
-        delta += S.tof_sigma * g;
-      }
-      const long long key_ = a_first ? bin_key(S, L.a_cr, L.b_cr, L.a_rg, L.b_rg, delta)
-                                     : bin_key(S, L.b_cr, L.a_cr, L.b_rg, L.a_rg, delta);
-      const bool scattered = (L.a_scat + L.nint) > 0;
-      const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
-      const bool take = cls == kScatter ? (J.bin_mask & 1) : cls == kTrue ? (J.bin_mask & 2) : false;
-      long long q = 0;
-      if (key_ >= 0 && (take || J.q_out)) {
-        float aa, ab, ba, bb;
-        angles(L.a_nx, L.a_ny, L.a_dir, aa, ab);
-        angles(L.b_nx, L.b_ny, L.dir, ba, bb);
-        const float w = lut_prob<DT>(J.lut, L.a_e, aa, ab, L.a_cr % S.module_t, L.a_rg % S.module_a) *
-                        lut_prob<DT>(J.lut, L.e, ba, bb, L.b_cr % S.module_t, L.b_rg % S.module_a);
-        q = __float2ll_rn(w * 4294967296.0f);
-      }
-      // lanes that hit the same bin add their weights first, one atomic per bin
-      const unsigned act = __activemask();
-      const unsigned takers = __ballot_sync(act, take);
-      if (take) {
-        const unsigned peers = __match_any_sync(takers, (unsigned long long)key_);
-        const unsigned hi = __reduce_add_sync(peers, (unsigned)(q >> 16));
-        const unsigned lo = __reduce_add_sync(peers, (unsigned)(q & 0xffff));
-        if (lane_id == (unsigned)(__ffs(peers) - 1)) {
-          atomicAdd(J.acc + key_, ((unsigned long long)hi << 16) + lo);
-          if (stats) atomicAdd(&s_cnt[kStatAtomics], 1ull);
-        }
-        if (stats) {
-          atomicAdd(&s_cnt[kStatBinned], 1ull);
-          atomicAdd(&s_cnt[kStatWeight], (unsigned long long)q);
-        }
-      }
-      finish(cls, key_, cls == kOutOfRange ? 0 : q);
-    }
-  }
-
-    __syncthreads();  // every lane is done with the chunk before the next fetch
+    __syncthreads();  // every slot is done with the chunk before the next fetch
   }
 
   if (!stats) return;
@@ -484,8 +563,8 @@ __global__ void __launch_bounds__(256, 3) transport_kernel(const __grid_constant
 }
 
 size_t transport_smem_bytes(const PhantomParams& ph, int block) {
-  return sizeof(uint32_t) * kRingWords * block + sizeof(float4) * (size_t)ph.n_mat * ph.n_tab +
-         sizeof(float) * (ph.n_tab + kMaxMaterials);
+  return sizeof(uint32_t) * kFields * (size_t)(block / 32) * kSlotsPerWarp +
+         sizeof(float4) * (size_t)ph.n_mat * ph.n_tab + sizeof(float) * (ph.n_tab + kMaxMaterials);
 }
 
 template <int DT>
