@@ -124,7 +124,7 @@ typedef struct {
   int32_t scanner, phantom, lut;   /* lut = 0: no LUT (every coincidence weighs 1) */
   int32_t acc;                     /* accumulator to add into */
   int32_t bin_mask;                /* PSC_BIN_SCATTER | PSC_BIN_TRUES; 0 = scatter */
-  int32_t block, grid;             /* launch shape: block a multiple of 32 in [32, 256]; 0 = automatic */
+  int32_t block, grid;             /* launch shape: block a multiple of 32 in [32, 512]; 0 = automatic */
   int8_t* cls_out;                 /* device [n_histories] history class, or NULL */
   int64_t* key_out;                /* device [n_histories] sinogram bin (-1 unless true/scatter), or NULL */
   int64_t* q_out;                  /* device [n_histories] fixed-point weight rint(w 2^32), or NULL */

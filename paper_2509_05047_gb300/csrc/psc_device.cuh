@@ -86,6 +86,7 @@ struct BatchParams {
   int n_jobs;
   unsigned long long* next_chunk;  // work counter, zero at launch
   unsigned long long* stats;       // kStatCount counters or nullptr
+  uint32_t* cold;                  // per-CTA slot fields kept out of shared memory
 };
 
 // ---------------------------------------------------------------------------

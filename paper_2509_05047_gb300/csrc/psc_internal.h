@@ -31,6 +31,8 @@ struct FinParams {
 int psc_set_error(int code, const char* fmt, ...);
 
 size_t transport_smem_bytes(const PhantomParams& ph, int block);
+// 32-bit words of the global slot buffer a launch of grid x block needs
+size_t transport_cold_words(int grid, int block);
 cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int block, size_t smem,
                              cudaStream_t s);
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm);

@@ -147,6 +147,11 @@ struct psc_ctx {
   // each zeroed on the launch's stream before use
   DevBuf counters;
   unsigned long long counter_next = 0;
+  // slot fields the transport kernel keeps in global memory, grown on
+  // demand; launches on different streams are ordered through cold_done
+  std::mutex cold_mu;
+  DevBuf cold;
+  cudaEvent_t cold_done = nullptr;
 };
 
 namespace {
@@ -326,7 +331,9 @@ int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
   }
   ctx->counters.bytes = sizeof(unsigned long long) * kCounterSlots;
   e = cudaEventCreateWithFlags(&ctx->scratch_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->cold_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
     delete ctx;
     return cuda_fail(e, "cudaEventCreate");
   }
@@ -339,6 +346,7 @@ void psc_destroy(psc_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
+  if (ctx->cold_done) cudaEventDestroy(ctx->cold_done);
   delete ctx;
 }
 
@@ -650,8 +658,8 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   if (acc->scanner != a->scanner) return fail(PSC_EINVAL, "accumulator belongs to scanner %d", (int)acc->scanner);
   if (a->first_history + a->n_histories < a->first_history) return fail(PSC_EOVERFLOW, "history range wraps");
   if (a->bin_mask < 0 || a->bin_mask > 3) return fail(PSC_EINVAL, "bin_mask must be in [0, 3]");
-  if (a->block < 0 || a->block > 256 || (a->block % 32) || a->grid < 0)
-    return fail(PSC_EINVAL, "block must be a multiple of 32 in [32, 256], grid >= 0");
+  if (a->block < 0 || a->block > 512 || (a->block % 32) || a->grid < 0)
+    return fail(PSC_EINVAL, "block must be a multiple of 32 in [32, 512], grid >= 0");
   const psc_phantom_desc& pd = ph->desc;
   const double R2 = sc->desc.radius * sc->desc.radius;
   for (int i = 0; i < 4; ++i) {
@@ -719,7 +727,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
   if (jobs.empty()) return PSC_OK;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int block = n > 0 && args[0].block ? args[0].block : 256;
+  const int block = n > 0 && args[0].block ? args[0].block : 512;
   std::unique_lock<std::mutex> lk(ctx->stats_mu, std::defer_lock);
   unsigned long long* dstats = nullptr;
   if (stats) {
@@ -764,7 +772,27 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s), "zero work counter");
     bp.next_chunk = counter;
     bp.stats = dstats;
+    std::lock_guard<std::mutex> cl(ctx->cold_mu);
+    const size_t cold_bytes = sizeof(uint32_t) * transport_cold_words(grid, block);
+    if (ctx->cold.bytes < cold_bytes) {
+      CK(cudaEventSynchronize(ctx->cold_done), "wait for the slot buffer's last user");
+      if (ctx->cold.p) {
+        cudaFree(ctx->cold.p);
+        ctx->cold.p = nullptr;
+        ctx->cold.bytes = 0;
+      }
+      cudaError_t e = cudaMalloc(&ctx->cold.p, cold_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cold.p = nullptr;
+        return fail(PSC_ENOMEM, "transport slot buffer of %zu bytes: %s", cold_bytes, cudaGetErrorString(e));
+      }
+      ctx->cold.bytes = cold_bytes;
+    }
+    bp.cold = (uint32_t*)ctx->cold.p;
+    CK(cudaStreamWaitEvent(s, ctx->cold_done, 0), "order slot buffer users");
     CK(launch_transport(bp, dt, grid, block, smem, s), "transport kernel launch");
+    CK(cudaEventRecord(ctx->cold_done, s), "order slot buffer users");
   }
   if (stats) {
     unsigned long long h[kStatCount];

@@ -8,9 +8,12 @@
 //        -> ESCAPE -> COINC -> next history
 //
 // Each warp owns a pool of kSlotsPerWarp photon slots whose state lives in
-// shared memory (structure of arrays).  Every loop iteration the warp votes
-// for the section that serves the most slots per cost, packs up to 32 slots
-// in that state onto its 32 lanes, and runs the section once for them.  With
+// shared memory (structure of arrays; the fields only emission, detection
+// and coincidence touch live in an L2-resident global buffer instead, which
+// leaves room for 32 warps per SM).  Every loop iteration the warp picks the
+// section that the most slots wait for (weighting sections by their cost
+// was measured slower, since it runs sections on fewer lanes), packs up to
+// 32 slots in that state onto its 32 lanes, and runs the section once.  With
 // twice as many slots as lanes the chosen section usually fills the warp,
 // where one history per lane left most lanes idle (the states of 32
 // histories spread over six sections).  The code holds a single copy of each
@@ -37,18 +40,25 @@ enum : int {
 
 constexpr int kSlotsPerWarp = 64;
 
-// fields of a photon slot: field f of slot g at slots[f * n_slots + g]
+// fields of a photon slot kept in shared memory (used by every section):
+// field f of slot g at slots[f * n_slots + g]
 enum : int {
   F_PX, F_PY, F_PZ, F_DX, F_DY, F_DZ, F_E, F_PATH,          // the photon in flight
   F_K, F_NB, F_HLO, F_HHI, F_META, F_CNT, F_TRIES,          // stream position, history, state
-  F_E0X, F_E0Y, F_E0Z, F_D0X, F_D0Y, F_D0Z,                 // emission point, photon A direction
-  F_ACRG, F_AE, F_APATH, F_ANX, F_ANY, F_ADX, F_ADY, F_ADZ,  // photon A at the detector
-  F_BCRG, F_BNX, F_BNY,                                      // photon B at the detector
   F_RING,                                                    // kRingWords words of the sub-stream
   kFields = F_RING + kRingWords
 };
+// fields read and written only at emission, detection and coincidence, kept
+// in an L2-resident global buffer: field f of slot g of CTA b at
+// cold[(b * kColdFields + f) * n_slots + g]
+enum : int {
+  C_E0X, C_E0Y, C_E0Z, C_D0X, C_D0Y, C_D0Z,                 // emission point, photon A direction
+  C_ACRG, C_AE, C_APATH, C_ANX, C_ANY, C_ADX, C_ADY, C_ADZ,  // photon A at the detector
+  C_BCRG, C_BNX, C_BNY,                                      // photon B at the detector
+  kColdFields
+};
 // F_META = state | photon << 3 | stream << 4;  F_CNT = steps | interactions << 16;
-// F_ACRG = crystal | ring << 16 | scattered << 31;  F_BCRG = crystal | ring << 16;
+// C_ACRG = crystal | ring << 16 | scattered << 31;  C_BCRG = crystal | ring << 16;
 // F_TRIES = tries (| material << 16 for a pending Rayleigh event)
 __host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
   return (uint32_t)state | (uint32_t)photon << 3 | (uint32_t)stream << 4;
@@ -99,7 +109,7 @@ __device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alph
 
 
 template <int DT>
-__global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant__ BatchParams B) {
+__global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ float4 smem[];
   const unsigned tid = threadIdx.x, bdim = blockDim.x;
   const int n_slots = (int)(bdim >> 5) * kSlotsPerWarp;
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
   __shared__ unsigned long long s_lo;         // first history of the chunk
   __shared__ unsigned s_len, s_next;          // chunk length, next offset to hand out
   __shared__ unsigned long long s_cnt[kStatCount];
-  __shared__ int s_sel[8][32];                // per warp: slot of each lane this iteration
+  __shared__ int s_sel[16][32];               // per warp: slot of each lane this iteration
   for (int i = tid; i < kStatCount; i += bdim) s_cnt[i] = 0;
   const unsigned lane_id = tid & 31u;
   const int warp = (int)(tid >> 5);
@@ -121,6 +131,10 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
   auto U = [&](int f, int g) -> uint32_t& { return slots[f * n_slots + g]; };
   auto Fv = [&](int f, int g) -> float { return __uint_as_float(slots[f * n_slots + g]); };
   auto setF = [&](int f, int g, float v) { slots[f * n_slots + g] = __float_as_uint(v); };
+  uint32_t* cold = B.cold + (size_t)blockIdx.x * kColdFields * n_slots;
+  auto CU = [&](int f, int g) -> uint32_t& { return cold[f * n_slots + g]; };
+  auto Cv = [&](int f, int g) -> float { return __uint_as_float(cold[f * n_slots + g]); };
+  auto setC = [&](int f, int g, float v) { cold[f * n_slots + g] = __float_as_uint(v); };
 
   for (;;) {
     // ---- fetch the next chunk of (job, history range) ----
@@ -204,9 +218,6 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
     start(g1);
     __syncwarp();
 
-    // per-section cost weights of the warp scheduler (1024 / approximate
-    // instructions of one execution of the section)
-    constexpr int kW[kNumSections] = {1024 / 140, 1024 / 90, 1024 / 70, 1024 / 60, 1024 / 80, 1024 / 300};
     // words a section reads, one nibble per section: 7, 2, 4, 3, 0, 2
     constexpr uint32_t kNeedNibbles = 0x203427u;
 
@@ -214,14 +225,14 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
       const int st0 = (int)(U(F_META, g0) & 7u), st1 = (int)(U(F_META, g1) & 7u);
       if (!__any_sync(0xffffffffu, st0 != kDone || st1 != kDone)) break;
 
-      // ---- warp vote: the section that serves the most slots per cost ----
+      // ---- warp vote: the section that the most slots wait for ----
       int sec = -1, best = 0;
       unsigned sm0 = 0, sm1 = 0;
 #pragma unroll
       for (int q = 0; q < kNumSections; ++q) {
         const unsigned m0 = __ballot_sync(0xffffffffu, st0 == q);
         const unsigned m1 = __ballot_sync(0xffffffffu, st1 == q);
-        const int score = min(32, __popc(m0) + __popc(m1)) * kW[q];
+        const int score = __popc(m0) + __popc(m1);
         if (score > best) {
           best = score;
           sec = q;
@@ -283,12 +294,12 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
           sincospif(2.0f * uni(6), &sp, &cp);
           const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
           const float dx = st * cp, dy = st * sp, dz = ct;
-          setF(F_E0X, g, ex);
-          setF(F_E0Y, g, ey);
-          setF(F_E0Z, g, ez);
-          setF(F_D0X, g, dx);
-          setF(F_D0Y, g, dy);
-          setF(F_D0Z, g, dz);
+          setC(C_E0X, g, ex);
+          setC(C_E0Y, g, ey);
+          setC(C_E0Z, g, ez);
+          setC(C_D0X, g, dx);
+          setC(C_D0Y, g, dy);
+          setC(C_D0Z, g, dz);
           setF(F_PX, g, ex);
           setF(F_PY, g, ey);
           setF(F_PZ, g, ez);
@@ -468,32 +479,32 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
             finish(g, cls, -1, 0);
           } else if (((m >> 3) & 1u) == 0) {  // photon A: keep it, launch photon B back to back
             const uint32_t nint = U(F_CNT, g) >> 16;
-            U(F_ACRG, g) = (uint32_t)cr | (uint32_t)rg << 16 | (nint > 0 ? 1u << 31 : 0u);
-            setF(F_AE, g, e);
-            setF(F_APATH, g, path);
-            setF(F_ANX, g, nx);
-            setF(F_ANY, g, ny);
-            setF(F_ADX, g, dx);
-            setF(F_ADY, g, dy);
-            setF(F_ADZ, g, dz);
-            setF(F_PX, g, Fv(F_E0X, g));
-            setF(F_PY, g, Fv(F_E0Y, g));
-            setF(F_PZ, g, Fv(F_E0Z, g));
-            setF(F_DX, g, -Fv(F_D0X, g));
-            setF(F_DY, g, -Fv(F_D0Y, g));
-            setF(F_DZ, g, -Fv(F_D0Z, g));
+            CU(C_ACRG, g) = (uint32_t)cr | (uint32_t)rg << 16 | (nint > 0 ? 1u << 31 : 0u);
+            setC(C_AE, g, e);
+            setC(C_APATH, g, path);
+            setC(C_ANX, g, nx);
+            setC(C_ANY, g, ny);
+            setC(C_ADX, g, dx);
+            setC(C_ADY, g, dy);
+            setC(C_ADZ, g, dz);
+            setF(F_PX, g, Cv(C_E0X, g));
+            setF(F_PY, g, Cv(C_E0Y, g));
+            setF(F_PZ, g, Cv(C_E0Z, g));
+            setF(F_DX, g, -Cv(C_D0X, g));
+            setF(F_DY, g, -Cv(C_D0Y, g));
+            setF(F_DZ, g, -Cv(C_D0Z, g));
             setF(F_E, g, kEmitKeV);
             setF(F_PATH, g, 0.0f);
             U(F_CNT, g) = 0;
             U(F_K, g) = 0;
             U(F_NB, g) = 0;
             U(F_META, g) = meta(kStep, 1, 2);
-          } else if (cr == (int)(U(F_ACRG, g) & 0xffffu)) {
+          } else if (cr == (int)(CU(C_ACRG, g) & 0xffffu)) {
             finish(g, kSameCrystal, -1, 0);
           } else {
-            U(F_BCRG, g) = (uint32_t)cr | (uint32_t)rg << 16;
-            setF(F_BNX, g, nx);
-            setF(F_BNY, g, ny);
+            CU(C_BCRG, g) = (uint32_t)cr | (uint32_t)rg << 16;
+            setC(C_BNX, g, nx);
+            setC(C_BNY, g, ny);
             setF(F_PATH, g, path);
             if (blur) {  // the TOF blur reads stream 0, block 2
               U(F_META, g) = meta(kCoinc, 1, 0);
@@ -507,10 +518,10 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
 
         // ---- coincidence: TOF, LOR bin, LUT weight, accumulate ----
         if (sec == kCoinc) {
-          const uint32_t acrg = U(F_ACRG, g), bcrg = U(F_BCRG, g);
+          const uint32_t acrg = CU(C_ACRG, g), bcrg = CU(C_BCRG, g);
           const int a_cr = (int)(acrg & 0xffffu), a_rg = (int)((acrg >> 16) & 0x7fffu);
           const int b_cr = (int)(bcrg & 0xffffu), b_rg = (int)(bcrg >> 16);
-          const float a_path = Fv(F_APATH, g), path = Fv(F_PATH, g);
+          const float a_path = Cv(C_APATH, g), path = Fv(F_PATH, g);
           const bool a_first = a_cr < b_cr;
           float delta = 0.5f * (a_first ? a_path - path : path - a_path);
           if (blur) {
@@ -525,9 +536,9 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
           long long q = 0;
           if (key_ >= 0 && (take || J.q_out)) {
             float aa, ab, ba, bb;
-            angles(Fv(F_ANX, g), Fv(F_ANY, g), make_float3(Fv(F_ADX, g), Fv(F_ADY, g), Fv(F_ADZ, g)), aa, ab);
-            angles(Fv(F_BNX, g), Fv(F_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
-            const float w = lut_prob<DT>(J.lut, Fv(F_AE, g), aa, ab, a_cr % S.module_t, a_rg % S.module_a) *
+            angles(Cv(C_ANX, g), Cv(C_ANY, g), make_float3(Cv(C_ADX, g), Cv(C_ADY, g), Cv(C_ADZ, g)), aa, ab);
+            angles(Cv(C_BNX, g), Cv(C_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
+            const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_cr % S.module_t, a_rg % S.module_a) *
                             lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_cr % S.module_t, b_rg % S.module_a);
             q = __float2ll_rn(w * 4294967296.0f);
           }
@@ -560,6 +571,10 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const __grid_constant
   __syncthreads();
   for (int i = threadIdx.x; i < kStatCount; i += blockDim.x)
     if (s_cnt[i]) atomicAdd(B.stats + i, s_cnt[i]);
+}
+
+size_t transport_cold_words(int grid, int block) {
+  return (size_t)grid * kColdFields * (size_t)(block / 32) * kSlotsPerWarp;
 }
 
 size_t transport_smem_bytes(const PhantomParams& ph, int block) {

@@ -71,7 +71,7 @@ def test_unit_lut_count_sinogram_is_bit_exact_on_matched_histories(tiny):
 def test_result_independent_of_launch_shape_and_partition(tiny):
     n = 150_001
     ref = None
-    for block, grid in [(256, 0), (64, 7), (128, 1000), (256, 3), (32, 152 * 40)]:
+    for block, grid in [(512, 0), (256, 0), (64, 7), (128, 1000), (256, 3), (32, 152 * 40)]:
         tiny.zero()
         tiny.run(SEED + 2, 5, n, listmode=False, block=block, grid=grid)
         a = tiny.acc()
@@ -163,7 +163,7 @@ def test_edge_cases(tiny):
     with pytest.raises(psc.PscError) as e:
         tiny.run(SEED, 0, 10, acc=tiny.l_id)                 # wrong object kind
     assert e.value.code == psc.PSC_ENOTFOUND
-    for block in (100, 512):
+    for block in (100, 1024):
         with pytest.raises(psc.PscError) as e:
             tiny.run(SEED, 0, 10, block=block)
         assert e.value.code == psc.PSC_EINVAL
