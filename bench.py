@@ -52,6 +52,9 @@ def parse():
                     help="profiling case: keep only this many rings (smaller sinogram)")
     ap.add_argument("--tof-bins", type=int, default=0,
                     help="profiling case: this many TOF bins over the same 648 mm range")
+    ap.add_argument("--precision-workload", default="small", choices=["small", "paper"],
+                    help="precision study on the small configuration (water cylinder, 288 x 16 "
+                         "scanner) or the paper-scale one")
     return ap.parse_args()
 
 
@@ -125,7 +128,7 @@ OPS_PER_HISTORY = 60
 # folded to one bin (the full 43.8 GB accumulator is too large to capture);
 # the traffic is the binned atomics and LUT misses, so it scales with the
 # histories of a launch
-TRANSPORT_DRAM_BYTES_PER_HISTORY = 112.49e6 / 2e7
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.76e6 + 22.64e6) / 2e7
 # algorithmic HBM bytes per bin of the smoothing finalize: radial 8 + 4,
 # view 4 + 4, axial 4 + 8 (per-LOR sensitivity reads are 8 / n_tof more)
 FINALIZE_BYTES_PER_BIN = 32
@@ -350,7 +353,14 @@ def run_precision(a):
     import paper_2509_05047_gb300 as psc
     from paper_2509_05047_gb300 import build as B
     B.build()
-    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins)
+    if a.precision_workload == "paper":
+        sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins)
+        workload = WORKLOAD
+    else:
+        sc, mats, ph = W.scanner_tiny(), W.standard_materials(), W.phantom_water_cylinder()
+        lut, sens = W.lut_tiny(sc), W.sensitivity_uniform(sc.lor_shape, seed=1)
+        workload = ("small: water cylinder r=100 mm in 64x64x32 voxels of 4 mm, scanner 288x16, "
+                    "13 TOF bins, LUT 16x8x8x4x4, smoothing sigma=2, per-LOR sensitivity")
     dev = torch.device("cuda", 0)
     ctx = psc.psc_create(0)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
@@ -397,7 +407,7 @@ def run_precision(a):
             rows.append({"histories": n, "lut": name, "rel_rms_vs_reference": rel_rms(out, ref),
                          "rel_rms_vs_f32_same_histories": rel_rms(out, base)})
     psc.psc_destroy(ctx)
-    return {"mode": "precision", "workload": WORKLOAD, "reference_histories": n_ref,
+    return {"mode": "precision", "workload": workload, "reference_histories": n_ref,
             "reference_seconds": t_ref, "smoothing_sigma_bins": sigma,
             "metric": "relative RMS sqrt(sum (A-B)^2 / sum B^2) over all bins after smoothing",
             "rows": rows}
