@@ -262,7 +262,7 @@ def run_native(a):
     roofline = {"bound": "alu", "achieved": round(achieved / 1e9, 1), "peak": round(peak_ops / 1e9, 1),
                 "unit": "Gop/s", "frac": round(achieved / peak_ops, 4),
                 "traffic": int(TRANSPORT_DRAM_BYTES_PER_HISTORY * n),
-                "kernel": "psc::transport_kernel<0>", "kernel_ms": round(kern_ms, 3),
+                "kernel": "psc::transport_kernel<0, false>", "kernel_ms": round(kern_ms, 3),
                 "peak_source": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)"}
     # the three smoothing passes together, against the measured copy bandwidth
     fin_gbs = FINALIZE_BYTES_PER_BIN * sc.n_bins / (phase[2] / 1e3) / 1e9

@@ -108,7 +108,9 @@ __device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alph
 }
 
 
-template <int DT>
+// kDebug: statistics counters and per-history listmode outputs are compiled
+// in only when a launch asks for them, so the production loop stays small
+template <int DT, bool kDebug>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ float4 smem[];
   const unsigned tid = threadIdx.x, bdim = blockDim.x;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
   const unsigned lane_id = tid & 31u;
   const int warp = (int)(tid >> 5);
   const int g0 = warp * kSlotsPerWarp + (int)lane_id, g1 = g0 + 32;  // the slots this lane refills
-  const bool stats = B.stats != nullptr;
+  const bool stats = kDebug && B.stats != nullptr;
   int cached = -1;
 
   auto U = [&](int f, int g) -> uint32_t& { return slots[f * n_slots + g]; };
@@ -207,10 +209,12 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     auto finish = [&](int g, int cls, long long key_out, long long q_out) {
       const unsigned long long h = (unsigned long long)U(F_HHI, g) << 32 | U(F_HLO, g);
       const unsigned long long i = h - J.first;
-      if (J.cls_out) J.cls_out[i] = (int8_t)cls;
-      if (J.key_out) J.key_out[i] = key_out;
-      if (J.q_out) J.q_out[i] = q_out;
-      if (stats) atomicAdd(&s_cnt[kStatClass0 + cls], 1ull);
+      if (kDebug) {
+        if (J.cls_out) J.cls_out[i] = (int8_t)cls;
+        if (J.key_out) J.key_out[i] = key_out;
+        if (J.q_out) J.q_out[i] = q_out;
+        if (stats) atomicAdd(&s_cnt[kStatClass0 + cls], 1ull);
+      }
       start(g);
     };
 
@@ -534,7 +538,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
           const bool take = cls == kScatter ? (J.bin_mask & 1) : cls == kTrue ? (J.bin_mask & 2) : false;
           long long q = 0;
-          if (key_ >= 0 && (take || J.q_out)) {
+          if (key_ >= 0 && (take || (kDebug && J.q_out))) {
             float aa, ab, ba, bb;
             angles(Cv(C_ANX, g), Cv(C_ANY, g), make_float3(Cv(C_ADX, g), Cv(C_ADY, g), Cv(C_ADZ, g)), aa, ab);
             angles(Cv(C_BNX, g), Cv(C_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
@@ -582,13 +586,20 @@ size_t transport_smem_bytes(const PhantomParams& ph, int block) {
          sizeof(float4) * (size_t)ph.n_mat * ph.n_tab + sizeof(float) * (ph.n_tab + kMaxMaterials);
 }
 
-template <int DT>
+template <int DT, bool kDebug>
 static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT>,
+  cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT, kDebug>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  transport_kernel<DT><<<grid, block, smem, s>>>(p);
+  transport_kernel<DT, kDebug><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t smem, cudaStream_t s) {
+  bool debug = p.stats != nullptr;
+  for (int j = 0; j < p.n_jobs; ++j) debug |= p.jobs[j].cls_out || p.jobs[j].key_out || p.jobs[j].q_out;
+  return debug ? launch_dt<DT, true>(p, grid, block, smem, s) : launch_dt<DT, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int block, size_t smem,
@@ -601,12 +612,13 @@ cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int 
   }
 }
 
+// both instantiations of a LUT type share launch bounds and shared memory
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm) {
   switch (lut_dtype) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<0>, block, smem);
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<1>, block, smem);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<2>, block, smem);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<-1>, block, smem);
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<0, false>, block, smem);
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<1, false>, block, smem);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<2, false>, block, smem);
+    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<-1, false>, block, smem);
   }
 }
 
