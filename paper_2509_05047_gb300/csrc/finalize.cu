@@ -144,6 +144,12 @@ __device__ __forceinline__ float f64_to_f32(double d) {
   return __uint_as_float(((hi & 0x80000000u) | ((unsigned)e << 23) | m) + up);
 }
 
+// a sinogram factor in FP32: from the FP32 copy when there is one, else
+// rounded from the FP64 values
+__device__ __forceinline__ float factor(const float* f32, const double* f64, long long i) {
+  return f32 ? __ldg(f32 + i) : f64_to_f32(__ldg(f64 + i));
+}
+
 // a * b (RNE) for finite doubles
 __device__ __forceinline__ double dmul(double a, double b) {
   const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
@@ -186,7 +192,8 @@ __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // the sliding window down one column of n rows; row r of the source is
 // src[r * stride] (rows outside [0, n) reflect).  cvt(raw, r) -> float;
-// store(r, value).  Each output is the FMA chain sum_j g[j] * x[o - KT + j],
+// store(o0, s[NB]) receives the outputs o0 .. o0 + NB - 1 of a step (those
+// below n are real).  Each output is the FMA chain sum_j g[j] * x[o - KT + j],
 // j = 0 .. 2 KT, in increasing j.  The NB loads of a step are issued before
 // any of them is converted, and rows are reflected only in the edge steps.
 // ---------------------------------------------------------------------------
@@ -220,13 +227,14 @@ __device__ __forceinline__ void slide(const In* __restrict__ src, long long stri
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) w[2 * KT + q] = cvt(raw[q], rr[q]);
+    float s[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-      float s = 0.0f;
+      s[q] = 0.0f;
 #pragma unroll
-      for (int j = 0; j <= 2 * KT; ++j) s = fmaf(g[j], w[q + j], s);
-      if (o0 + q < n) store(o0 + q, s);
+      for (int j = 0; j <= 2 * KT; ++j) s[q] = fmaf(g[j], w[q + j], s[q]);
     }
+    store(o0, s);
 #pragma unroll
     for (int j = 0; j < 2 * KT; ++j) w[j] = w[NB + j];
   }
@@ -236,13 +244,17 @@ __device__ __forceinline__ void slide(const In* __restrict__ src, long long stri
 template <class In, class Cvt, class Store>
 __device__ __forceinline__ void slide_generic(const In* __restrict__ src, long long stride, int n, int K,
                                               const Weights& g, Cvt cvt, Store store) {
-  for (int o = 0; o < n; ++o) {
-    float s = 0.0f;
-    for (int j = 0; j <= 2 * K; ++j) {
-      const int r = reflect(o - K + j, n);
-      s = fmaf(g[j], cvt(__ldg(src + r * stride), r), s);
+  for (int o0 = 0; o0 < n; o0 += NB) {
+    float s[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      s[q] = 0.0f;
+      for (int j = 0; j <= 2 * K; ++j) {
+        const int r = reflect(o0 + q - K + j, n);
+        s[q] = fmaf(g[j], cvt(__ldg(src + r * stride), r), s[q]);
+      }
     }
-    store(o, s);
+    store(o0, s);
   }
 }
 
@@ -274,12 +286,16 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
     float x = i64_to_f32(q) * cf;
     if (per_bin_factor) {
       const long long bin = base + (long long)r * T, lor = line * R + r;
-      if (P.sens_first && P.sens) x *= f64_to_f32(at(P.sens, P.sens_per_lor ? lor : bin));
-      if (P.norm) x *= f64_to_f32(at(P.norm, P.norm_per_lor ? lor : bin));
+      if (P.sens_first && P.sens) x *= factor(P.sens32, P.sens, P.sens_per_lor ? lor : bin);
+      if (P.norm) x *= factor(P.norm32, P.norm, P.norm_per_lor ? lor : bin);
     }
     return x;
   };
-  auto store = [&](int r, float y) { dst[r * T] = y; };
+  auto store = [&](int r0, const float (&y)[NB]) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (r0 + q < R) dst[(r0 + q) * T] = y[q];
+  };
   slide_any<KT>(P.acc + base, T, R, P.K[0], P.g[0], cvt, store);
 }
 
@@ -296,8 +312,13 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
   const float* src = reinterpret_cast<const float*>(P.out) + base;
   float* dst = P.scratch + base;
   auto cvt = [](float x, int) { return x; };
-  auto store = [&](int v, float y) { dst[v * I] = y; };
-  slide_any<KT>(src, I, P.V, P.K[1], P.g[1], cvt, store);
+  const int V = P.V;
+  auto store = [&](int v0, const float (&y)[NB]) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (v0 + q < V) dst[(v0 + q) * I] = y[q];
+  };
+  slide_any<KT>(src, I, V, P.K[1], P.g[1], cvt, store);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,26 +344,49 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
   const long long lor0 = p0 * lors + (long long)v * P.R + fdiv((unsigned)i, P.magic_T);
   const long long lor_step = (long long)(nr + 1) * lors;
   auto cvt = [](float x, int) { return x; };
-  auto store = [&](int k, float o) {
-    const long long bin = bin0 + k * bin_step;
-    const long long lor = lor0 + k * lor_step;
-    // the smoothed value carries FP32 precision: the factors are rounded to
-    // FP32, multiplied in FP32 and the result widened exactly to FP64
-    float y = o;
-    if (P.rnorm) y *= f64_to_f32(at(P.rnorm, P.norm_per_lor ? lor : bin));
-    if (!P.sens_first && P.sens) y *= f64_to_f32(at(P.sens, P.sens_per_lor ? lor : bin));
-    P.out[bin] = f32_to_f64(y);
+  const bool use_rnorm = P.rnorm || P.rnorm32, use_sens = !P.sens_first && P.sens;
+  // the smoothed value carries FP32 precision: the factors are FP32 (rounded
+  // once), multiplied in FP32 and the result widened exactly to FP64.  The
+  // factor loads of a step are issued before any output is stored.
+  auto store = [&](int k0, const float (&o)[NB]) {
+    const long long b0 = bin0 + k0 * bin_step, l0 = lor0 + k0 * lor_step;
+    float fr[NB], fs[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const long long bin = b0 + q * bin_step, lor = l0 + q * lor_step;
+      const bool in = k0 + q < L;
+      fr[q] = use_rnorm && in ? factor(P.rnorm32, P.rnorm, P.norm_per_lor ? lor : bin) : 1.0f;
+      fs[q] = use_sens && in ? factor(P.sens32, P.sens, P.sens_per_lor ? lor : bin) : 1.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (k0 + q >= L) break;
+      float y = o[q];
+      if (use_rnorm) y *= fr[q];
+      if (use_sens) y *= fs[q];
+      P.out[b0 + q * bin_step] = f32_to_f64(y);
+    }
   };
   slide_any<KT>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
 }
 
-// reciprocal of a normalisation sinogram, 0 where it is 0
-__global__ void reciprocal_kernel(const double* __restrict__ a, double* __restrict__ r, long long n) {
+// reciprocal of a normalisation sinogram, 0 where it is 0: FP64 (r) and/or
+// rounded to FP32 (r32)
+__global__ void reciprocal_kernel(const double* __restrict__ a, double* __restrict__ r, float* __restrict__ r32,
+                                  long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double v = a[i];
-    r[i] = v != 0.0 ? 1.0 / v : 0.0;
+    const double x = v != 0.0 ? 1.0 / v : 0.0;
+    if (r) r[i] = x;
+    if (r32) r32[i] = f64_to_f32(x);
   }
+}
+
+// FP32 copy of a sinogram (round to nearest even)
+__global__ void narrow_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = f64_to_f32(a[i]);
 }
 
 static int grid_for(long long n, int block, int sms) {
@@ -351,8 +395,13 @@ static int grid_for(long long n, int block, int sms) {
   return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
-cudaError_t launch_reciprocal(const double* a, double* r, long long n, int sms, cudaStream_t s) {
-  reciprocal_kernel<<<grid_for(n, 256, sms), 256, 0, s>>>(a, r, n);
+cudaError_t launch_reciprocal(const double* a, double* r, float* r32, long long n, int sms, cudaStream_t s) {
+  reciprocal_kernel<<<grid_for(n, 256, sms), 256, 0, s>>>(a, r, r32, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const double* a, float* b, long long n, int sms, cudaStream_t s) {
+  narrow_kernel<<<grid_for(n, 256, sms), 256, 0, s>>>(a, b, n);
   return cudaGetLastError();
 }
 

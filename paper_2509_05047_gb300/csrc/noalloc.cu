@@ -110,7 +110,7 @@ extern "C" int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t 
     p.norm = norm;
     p.norm_per_lor = norm_per_lor ? 1 : 0;
     p.rnorm = rnorm;
-    e = launch_reciprocal(norm, rnorm, n_norm, sms, s);
+    e = launch_reciprocal(norm, rnorm, nullptr, n_norm, sms, s);
     if (e != cudaSuccess) return psc_set_error(PSC_EDEVICE, "reciprocal: %s", cudaGetErrorString(e));
   }
   e = launch_finalize(p, sms, s);

@@ -16,6 +16,9 @@ struct FinParams {
   const double* sens;
   const double* norm;
   const double* rnorm;         // 1/norm, 0 where norm == 0
+  const float* sens32;         // FP32 copies (round to nearest) of sens, norm and 1/norm, or
+  const float* norm32;         // nullptr: the smoothing then rounds the FP64 values itself
+  const float* rnorm32;
   int sens_per_lor, norm_per_lor;
   double c;                    // scale * 2^-32
   long long n_bins;
@@ -41,6 +44,9 @@ cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* bloc
 // or an error code with the message set
 int finalize_plan(FinParams& p, const double sigma[3]);
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s);
-cudaError_t launch_reciprocal(const double* a, double* r, long long n, int sms, cudaStream_t s);
+// 1/a (0 where a == 0) into r (FP64) and/or r32 (FP32), either may be nullptr
+cudaError_t launch_reciprocal(const double* a, double* r, float* r32, long long n, int sms, cudaStream_t s);
+// FP32 copy of a sinogram, round to nearest even
+cudaError_t launch_narrow(const double* a, float* b, long long n, int sms, cudaStream_t s);
 
 }  // namespace psc

@@ -98,7 +98,7 @@ struct SinoObj : Object {
   int32_t scanner = 0;
   int per_lor = 0;
   long long n = 0;
-  DevBuf data, recip;
+  DevBuf data, data32, recip32;  // FP64 values, FP32 copy, FP32 reciprocal (made on first use)
   SinoObj() : Object(kSinoObj) {}
 };
 
@@ -580,8 +580,11 @@ int psc_load_sinogram(psc_ctx* ctx, int32_t scanner, const double* host, int32_t
   o->n = per_lor ? sc->n_lor : sc->n_bins;
   int rc;
   if ((rc = dev_alloc(ctx, o->data, sizeof(double) * o->n))) return rc;
-  o->bytes = o->data.bytes;
+  if ((rc = dev_alloc(ctx, o->data32, sizeof(float) * o->n))) return rc;
+  o->bytes = o->data.bytes + o->data32.bytes;
   CK(cudaMemcpy(o->data.p, host, sizeof(double) * o->n, cudaMemcpyHostToDevice), "upload sinogram");
+  CK(launch_narrow((const double*)o->data.p, (float*)o->data32.p, o->n, ctx->sms, 0), "FP32 copy of the sinogram");
+  CK(cudaStreamSynchronize(0), "FP32 copy of the sinogram");
   *id = add_object(ctx, o);
   return PSC_OK;
 }
@@ -842,6 +845,7 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
   p.acc = (const long long*)acc->data.p;
   p.out = out;
   p.sens = sens ? (const double*)sens->data.p : nullptr;
+  p.sens32 = sens ? (const float*)sens->data32.p : nullptr;
   p.sens_per_lor = sens ? sens->per_lor : 0;
   p.c = std::ldexp(a->scale, -32);
   p.n_bins = sc->n_bins;
@@ -865,12 +869,15 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
   if (norm) {
     p.norm = (const double*)norm->data.p;
     p.norm_per_lor = norm->per_lor;
-    if (!norm->recip.p) {
+    if (!norm->recip32.p) {
       int rc;
-      if ((rc = dev_alloc(ctx, norm->recip, sizeof(double) * norm->n))) return rc;
-      CK(launch_reciprocal((const double*)norm->data.p, (double*)norm->recip.p, norm->n, ctx->sms, s), "reciprocal");
+      if ((rc = dev_alloc(ctx, norm->recip32, sizeof(float) * norm->n))) return rc;
+      norm->bytes += norm->recip32.bytes;
+      CK(launch_reciprocal((const double*)norm->data.p, nullptr, (float*)norm->recip32.p, norm->n, ctx->sms, s),
+         "reciprocal");
     }
-    p.rnorm = (const double*)norm->recip.p;
+    p.rnorm32 = (const float*)norm->recip32.p;
+    p.norm32 = (const float*)norm->data32.p;
   }
   {
     std::lock_guard<std::mutex> lk(ctx->scratch_mu);
