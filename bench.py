@@ -29,6 +29,8 @@ import workloads as W  # noqa: E402
 METRIC = "photon histories/s"
 UNIT = "histories/s"
 WORKLOAD = "paper-scale torso 128x128x89, scanner 448x45, 27 TOF (400 ps), LUT 64x32x32x16x9 f32, 1e9 histories/step, smoothing sigma=2, per-LOR sensitivity"
+WORKLOAD_SMALL = ("small: water cylinder r=100 mm in 64x64x32 voxels of 4 mm, scanner 288x16, 13 TOF bins of 50 mm, "
+                  "LUT 16x8x8x4x4 f32, smoothing sigma=2, per-LOR sensitivity")
 
 
 def parse():
@@ -52,6 +54,8 @@ def parse():
                     help="profiling case: keep only this many rings (smaller sinogram)")
     ap.add_argument("--tof-bins", type=int, default=0,
                     help="profiling case: this many TOF bins over the same 648 mm range")
+    ap.add_argument("--workload", default="paper", choices=["paper", "small"],
+                    help="step workload: the paper-scale configuration or the small one")
     ap.add_argument("--precision-workload", default="small", choices=["small", "paper"],
                     help="precision study on the small configuration (water cylinder, 288 x 16 "
                          "scanner) or the paper-scale one")
@@ -146,7 +150,11 @@ def transport_ops(st):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
-def build_inputs(rings=0, tof_bins=0):
+def build_inputs(rings=0, tof_bins=0, workload="paper"):
+    if workload == "small":
+        sc = W.scanner_tiny()
+        return (sc, W.standard_materials(), W.phantom_water_cylinder(), W.lut_tiny(sc),
+                W.sensitivity_uniform(sc.lor_shape, seed=1))
     sc = W.scanner_signa()
     if rings:
         sc = W.Scanner(sc.radius, sc.n_crystals, rings, sc.ring_pitch, sc.module_t, sc.module_a,
@@ -176,7 +184,7 @@ def run_native(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins)
+    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins, a.workload)
     n = int(a.histories)
     ctx = psc.psc_create(local)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
@@ -270,13 +278,15 @@ def run_native(a):
                          "frac": round(fin_gbs / peaks["hbm_gbs"], 4), "traffic": None,
                          "kernels": "psc::smooth_{radial,view,axial}_kernel", "ms": round(float(phase[2]), 3),
                          "peak_source": f"{src} copy bandwidth"}
-    workload = WORKLOAD if not (a.rings or a.tof_bins) else \
-        f"profiling case: {WORKLOAD} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
+    base_wl = WORKLOAD_SMALL if a.workload == "small" else WORKLOAD
+    workload = base_wl if not (a.rings or a.tof_bins) else \
+        f"profiling case: {base_wl} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload, "histories_per_step": n, "global_batch": world * n,
-                      "l2": "inputs larger than L2 (43.8 GB accumulator + 43.8 GB output streamed every step)",
+                      "l2": f"inputs larger than L2 ({sc.n_bins * 8 / 1e9:.1f} GB accumulator + "
+                            f"{sc.n_bins * 8 / 1e9:.1f} GB output streamed every step)",
                       "parallelism": f"replicas{world}"},
            "roofline": roofline, "finalize_roofline": finalize_roofline, "clocks": clocks, "e2e": e2e,
            "gpu_launches": 4 * a.steps,
@@ -359,8 +369,7 @@ def run_precision(a):
     else:
         sc, mats, ph = W.scanner_tiny(), W.standard_materials(), W.phantom_water_cylinder()
         lut, sens = W.lut_tiny(sc), W.sensitivity_uniform(sc.lor_shape, seed=1)
-        workload = ("small: water cylinder r=100 mm in 64x64x32 voxels of 4 mm, scanner 288x16, "
-                    "13 TOF bins, LUT 16x8x8x4x4, smoothing sigma=2, per-LOR sensitivity")
+        workload = WORKLOAD_SMALL
     dev = torch.device("cuda", 0)
     ctx = psc.psc_create(0)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
