@@ -169,7 +169,11 @@ int psc_load_materials(psc_ctx* ctx, const psc_materials_desc* desc, int32_t* id
  * Woodcock majorant for this phantom. */
 int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* desc, int32_t materials, int32_t* id);
 /* New activity image for a loaded phantom (joint activity/scatter
- * estimation, Sec. 2.3.3 step 2): rebuilds the alias table only. */
+ * estimation, Sec. 2.3.3 step 2): rebuilds the alias table only.  Builds it
+ * on the host, waits (host-side) for the transport launches issued so far
+ * that read this phantom, then uploads it; other device work, on any
+ * stream, keeps running.  Launches issued after the call returns use the
+ * new image. */
 int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity /* host */);
 /* Copy a phantom's resident emission alias table to host arrays of n_vox
  * entries: column v is kept when (x >> 9) < threshold[v] for the Philox word

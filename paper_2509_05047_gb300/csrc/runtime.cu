@@ -84,7 +84,14 @@ struct PhantomObj : Object {
   int n_mat = 0, n_e = 0;
   long long n_vox = 0;
   DevBuf vox, alias, xs, maj, kappa;
+  // completes after every transport launch so far that reads this phantom
+  // (each launch's record first waits for the previous one)
+  std::mutex use_mu;
+  cudaEvent_t last_use = nullptr;
   PhantomObj() : Object(kPhantomObj) {}
+  ~PhantomObj() override {
+    if (last_use) cudaEventDestroy(last_use);
+  }
 };
 
 struct LutObj : Object {
@@ -152,6 +159,7 @@ struct psc_ctx {
   std::mutex cold_mu;
   DevBuf cold;
   cudaEvent_t cold_done = nullptr;
+  cudaStream_t upload = nullptr;  // non-blocking stream of alias-table uploads
 };
 
 namespace {
@@ -332,8 +340,10 @@ int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
   ctx->counters.bytes = sizeof(unsigned long long) * kCounterSlots;
   e = cudaEventCreateWithFlags(&ctx->scratch_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->cold_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
+    if (ctx->cold_done) cudaEventDestroy(ctx->cold_done);
     delete ctx;
     return cuda_fail(e, "cudaEventCreate");
   }
@@ -347,6 +357,7 @@ void psc_destroy(psc_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
   if (ctx->cold_done) cudaEventDestroy(ctx->cold_done);
+  if (ctx->upload) cudaStreamDestroy(ctx->upload);
   delete ctx;
 }
 
@@ -414,6 +425,9 @@ static uint32_t alias_threshold(double p) {
   return t >= 8388608.0 ? 8388608u : (uint32_t)t;
 }
 
+// builds the alias table on the host, waits for the launches still reading
+// the phantom's current table, then uploads on the context's own
+// non-blocking stream (so work on other streams keeps running)
 static int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
   std::vector<double> prob;
   std::vector<int32_t> alias;
@@ -421,8 +435,11 @@ static int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
   if (rc) return rc;
   std::vector<uint2> tab((size_t)o->n_vox);
   for (long long i = 0; i < o->n_vox; ++i) tab[i] = make_uint2(alias_threshold(prob[i]), (uint32_t)alias[i]);
-  CK(cudaMemcpy(o->alias.p, tab.data(), sizeof(uint2) * o->n_vox, cudaMemcpyHostToDevice), "upload alias");
-  (void)ctx;
+  std::lock_guard<std::mutex> lk(o->use_mu);
+  if (o->last_use) CK(cudaEventSynchronize(o->last_use), "wait for launches reading the phantom");
+  CK(cudaMemcpyAsync(o->alias.p, tab.data(), sizeof(uint2) * o->n_vox, cudaMemcpyHostToDevice, ctx->upload),
+     "upload alias");
+  CK(cudaStreamSynchronize(ctx->upload), "upload alias");
   return PSC_OK;
 }
 
@@ -504,7 +521,6 @@ int psc_update_activity(psc_ctx* ctx, int32_t phantom, const float* activity) {
   if (!ctx || !activity) return fail(PSC_EINVAL, "NULL argument");
   GET(PhantomObj, ph, phantom, kPhantomObj);
   DeviceGuard g(ctx->device);
-  CK(cudaDeviceSynchronize(), "synchronize before activity update");
   return upload_alias(ctx, ph.get(), activity);
 }
 
@@ -716,6 +732,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
   if (!ctx || (!args && n > 0) || n < 0) return fail(PSC_EINVAL, "NULL argument or negative count");
   std::vector<Job> jobs;
   std::vector<int> dts;
+  std::vector<std::shared_ptr<PhantomObj>> phs;
   jobs.reserve(n);
   for (int i = 0; i < n; ++i) {
     Job jb;
@@ -725,6 +742,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     if (jb.n == 0) continue;
     jobs.push_back(jb);
     dts.push_back(dt);
+    phs.push_back(get<PhantomObj>(ctx, args[i].phantom, kPhantomObj));
   }
   if (stats) std::memset(stats, 0, sizeof *stats);
   if (jobs.empty()) return PSC_OK;
@@ -747,9 +765,11 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     size_t smem = 0;
     unsigned long long total = 0;
     const int dt = dts[i0];
+    std::vector<PhantomObj*> used;
     for (size_t i = i0; i < jobs.size() && bp.n_jobs < kMaxJobs; ++i) {
       if (done[i] || dts[i] != dt) continue;
       done[i] = true;
+      used.push_back(phs[i].get());
       bp.jobs[bp.n_jobs] = jobs[i];
       smem = std::max(smem, transport_smem_bytes(jobs[i].ph, block));
       ++bp.n_jobs;
@@ -796,6 +816,12 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     CK(cudaStreamWaitEvent(s, ctx->cold_done, 0), "order slot buffer users");
     CK(launch_transport(bp, dt, grid, block, smem, s), "transport kernel launch");
     CK(cudaEventRecord(ctx->cold_done, s), "order slot buffer users");
+    for (PhantomObj* ph : used) {  // activity updates wait for this launch
+      std::lock_guard<std::mutex> ul(ph->use_mu);
+      if (!ph->last_use) CK(cudaEventCreateWithFlags(&ph->last_use, cudaEventDisableTiming), "phantom event");
+      else CK(cudaStreamWaitEvent(s, ph->last_use, 0), "order phantom users");
+      CK(cudaEventRecord(ph->last_use, s), "phantom event");
+    }
   }
   if (stats) {
     unsigned long long h[kStatCount];
