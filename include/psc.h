@@ -259,7 +259,8 @@ typedef struct {
   int32_t sens_first;
   double* out;                     /* device f64, the scanner's sinogram size; written on the
                                       server's streams, so no other work may be pending on it */
-  const float* activity;           /* host [n_vox] new activity image, copied at submit; NULL keeps */
+  const float* activity;           /* host [n_vox] new activity image; its alias table is built by
+                                      psc_submit on the calling thread; NULL keeps the current one */
 } psc_request;
 
 typedef struct {

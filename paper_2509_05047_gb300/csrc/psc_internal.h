@@ -5,7 +5,11 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "psc_device.cuh"
+
+struct psc_ctx;
 
 namespace psc {
 
@@ -32,6 +36,12 @@ struct FinParams {
 
 // sets the calling thread's psc_last_error() message, returns code
 int psc_set_error(int code, const char* fmt, ...);
+
+// the emission alias table of an activity image, built on the host
+int alias_table(const float* activity, long long n_vox, std::vector<uint2>& tab);
+// installs a prepared alias table: waits for the launches reading the
+// phantom's current one, then uploads
+int put_alias(psc_ctx* ctx, int32_t phantom, const uint2* tab, long long n_vox);
 
 size_t transport_smem_bytes(const PhantomParams& ph, int block);
 // 32-bit words of the global slot buffer a launch of grid x block needs

@@ -425,23 +425,57 @@ static uint32_t alias_threshold(double p) {
   return t >= 8388608.0 ? 8388608u : (uint32_t)t;
 }
 
-// builds the alias table on the host, waits for the launches still reading
-// the phantom's current table, then uploads on the context's own
-// non-blocking stream (so work on other streams keeps running)
-static int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
+}  // extern "C"
+
+namespace psc {
+
+int alias_table(const float* activity, long long n_vox, std::vector<uint2>& tab) {
   std::vector<double> prob;
   std::vector<int32_t> alias;
-  int rc = build_alias(activity, o->n_vox, prob, alias);
+  int rc = build_alias(activity, n_vox, prob, alias);
   if (rc) return rc;
-  std::vector<uint2> tab((size_t)o->n_vox);
-  for (long long i = 0; i < o->n_vox; ++i) tab[i] = make_uint2(alias_threshold(prob[i]), (uint32_t)alias[i]);
+  tab.resize((size_t)n_vox);
+  for (long long i = 0; i < n_vox; ++i) tab[i] = make_uint2(alias_threshold(prob[i]), (uint32_t)alias[i]);
+  return PSC_OK;
+}
+
+}  // namespace psc
+
+namespace {
+
+// waits for the launches still reading the phantom's current table, then
+// uploads on the context's own non-blocking stream (so work on other
+// streams keeps running)
+int put_alias_obj(psc_ctx* ctx, PhantomObj* o, const uint2* tab) {
   std::lock_guard<std::mutex> lk(o->use_mu);
   if (o->last_use) CK(cudaEventSynchronize(o->last_use), "wait for launches reading the phantom");
-  CK(cudaMemcpyAsync(o->alias.p, tab.data(), sizeof(uint2) * o->n_vox, cudaMemcpyHostToDevice, ctx->upload),
+  CK(cudaMemcpyAsync(o->alias.p, tab, sizeof(uint2) * o->n_vox, cudaMemcpyHostToDevice, ctx->upload),
      "upload alias");
   CK(cudaStreamSynchronize(ctx->upload), "upload alias");
   return PSC_OK;
 }
+
+int upload_alias(psc_ctx* ctx, PhantomObj* o, const float* activity) {
+  std::vector<uint2> tab;
+  int rc = psc::alias_table(activity, o->n_vox, tab);
+  return rc ? rc : put_alias_obj(ctx, o, tab.data());
+}
+
+}  // namespace
+
+namespace psc {
+
+int put_alias(psc_ctx* ctx, int32_t phantom, const uint2* tab, long long n_vox) {
+  GET(PhantomObj, ph, phantom, kPhantomObj);
+  if (ph->n_vox != n_vox) return fail(PSC_EINVAL, "alias table of %lld entries for a phantom of %lld voxels", n_vox,
+                                      ph->n_vox);
+  DeviceGuard g(ctx->device);
+  return put_alias_obj(ctx, ph.get(), tab);
+}
+
+}  // namespace psc
+
+extern "C" {
 
 int psc_load_phantom(psc_ctx* ctx, const psc_phantom_desc* d, int32_t materials, int32_t* id) {
   if (!ctx || !id || !d) return fail(PSC_EINVAL, "NULL argument");

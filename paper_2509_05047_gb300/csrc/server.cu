@@ -39,7 +39,7 @@ enum { kWaiting = 0, kActive = 1, kFinalizing = 2, kDoneState = 3, kFailed = 4 }
 struct Request {
   uint64_t ticket = 0;
   psc_request r{};
-  std::vector<float> activity;   // copy of the new activity image (empty: keep)
+  std::vector<uint2> alias;      // alias table of the new activity image (empty: keep)
   uint64_t next = 0;             // histories already launched
   int32_t acc = 0;
   int state = kWaiting;
@@ -101,7 +101,7 @@ void Server::run() {
       while (!waiting.empty() && (int)(active.size() + cand.size()) < cfg.max_active) {
         auto q = waiting.front();
         bool busy = false;
-        if (!q->activity.empty()) {
+        if (!q->alias.empty()) {
           for (auto& a : active) busy |= a->r.phantom == q->r.phantom;
           for (auto& a : finalizing) busy |= a->r.phantom == q->r.phantom;
           for (auto& a : cand) busy |= a->r.phantom == q->r.phantom;
@@ -130,7 +130,7 @@ void Server::run() {
         }
       }
       q->acc = acc;
-      if (!rc && !q->activity.empty()) rc = psc_update_activity(ctx, q->r.phantom, q->activity.data());
+      if (!rc && !q->alias.empty()) rc = psc::put_alias(ctx, q->r.phantom, q->alias.data(), (long long)q->alias.size());
       if (!rc) rc = psc_acc_zero(ctx, acc, sc);
       std::lock_guard<std::mutex> lk(mu);
       if (rc) {
@@ -292,10 +292,12 @@ int psc_submit(psc_ctx* ctx, const psc_request* r, uint64_t* ticket) {
   auto q = std::make_shared<Request>();
   q->r = *r;
   if (r->activity) {
-    // copy now: the caller's buffer may change before the request is admitted
+    // the alias table is built now, on the caller's thread (the caller's
+    // buffer may change before admission, and the server thread only uploads)
     const int64_t nv = psc_phantom_voxels(ctx, r->phantom);
     if (nv <= 0) return psc::psc_set_error(PSC_ENOTFOUND, "no phantom with id %d", (int)r->phantom);
-    q->activity.assign(r->activity, r->activity + nv);
+    const int rc = psc::alias_table(r->activity, nv, q->alias);
+    if (rc) return rc;
   }
   if (cudaEventCreateWithFlags(&q->fin, cudaEventDisableTiming) != cudaSuccess)
     return psc::psc_set_error(PSC_EDEVICE, "cudaEventCreate");
