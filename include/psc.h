@@ -79,6 +79,10 @@ typedef struct {
   int32_t n_rad;        /* radial bins kept: centred clip of the n_crystals - 1 bins (same parity) */
   double tof_bin_mm;    /* w (mm) */
   double tof_sigma_mm;  /* Gaussian TOF blur sigma of (l_a - l_b)/2 (mm), 0 = none */
+  double e_res_fwhm;    /* energy resolution: FWHM as a fraction of 511 keV at 511 keV, scaling as
+                           sqrt(E) (the no-LUT mode of Sec. 2.2.1 uses 0.112 with a 425-650 keV
+                           window); 0 = exact energies.  The window tests the blurred energy; a
+                           Compton-scattered photon is dropped below e_lo - 5 sigma(e_lo). */
 } psc_scanner_desc;
 
 /* Materials: mass attenuation tables on the grid E = 0, 1, ..., n_e-1 keV

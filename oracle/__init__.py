@@ -50,7 +50,8 @@ class Scanner(C.Structure):
     _fields_ = [("radius", C.c_double), ("ring_pitch", C.c_double), ("n_crystals", C.c_int32),
                 ("n_rings", C.c_int32), ("module_t", C.c_int32), ("module_a", C.c_int32),
                 ("e_lo", C.c_double), ("e_hi", C.c_double), ("n_tof", C.c_int32),
-                ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double)]
+                ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double),
+                ("e_res", C.c_double)]
 
 
 class Materials(C.Structure):
@@ -86,7 +87,8 @@ class Record(C.Structure):
                 ("n_rayleigh", _I2), ("n_steps", _I2), ("energy", _D2), ("alpha", _D2),
                 ("beta", _D2), ("path", _D2), ("prob", _D2), ("hit", _D3 * 2),
                 ("exit_pos", _D3 * 2), ("exit_dir", _D3 * 2), ("c_e_before", C.c_double),
-                ("c_e_after", C.c_double), ("c_dir_before", _D3), ("c_dir_after", _D3)]
+                ("c_e_after", C.c_double), ("c_dir_before", _D3), ("c_dir_after", _D3),
+                ("e_det", _D2)]
 
 
 def _record_dtype():
@@ -162,7 +164,7 @@ class _Keep:
 def scanner_struct(sc):
     return _Keep(Scanner(sc.radius, sc.ring_pitch, sc.n_crystals, sc.n_rings, sc.module_t,
                          sc.module_a, sc.e_lo, sc.e_hi, sc.n_tof, sc.n_rad, sc.tof_bin_mm,
-                         sc.tof_sigma_mm))
+                         sc.tof_sigma_mm, getattr(sc, "e_res", 0.0)))
 
 
 def materials_struct(mats):

@@ -367,10 +367,25 @@ typedef struct {
   double pos[3], dir[3], e, path;
   int n_compton, n_rayleigh, n_steps;
   int crystal, ring;
-  double hit[3], alpha, beta, prob;
+  double hit[3], alpha, beta, prob, e_det;
   int have_c;
   double c_e_before, c_e_after, c_dir_before[3], c_dir_after[3];
 } photon_t;
+
+/* Energy resolution (the no-LUT mode of Sec. 2.2.1 uses 11.2 %): the
+ * detected energy is E + sigma(E) g, g standard normal (Box-Muller on two
+ * words of the photon's stream), sigma(E) = e_res sqrt(511 E) / 2.3548, so
+ * the FWHM is e_res * 511 keV at 511 keV and scales as sqrt(E).  A photon
+ * that Compton-scatters below e_lo - 5 sigma(e_lo) is dropped (without
+ * resolution: below e_lo, which is exact since E never increases). */
+static double e_sigma(const orc_scanner* sc, double e) {
+  return sc->e_res * sqrt(511.0 * e) / 2.3548200450309493;
+}
+
+static double e_kill(const orc_scanner* sc) {
+  if (!(sc->e_res > 0.0)) return sc->e_lo;
+  return fmax(0.0, sc->e_lo - 5.0 * e_sigma(sc, sc->e_lo));
+}
 
 static void track_photon(const sim_ctx* X, stream_t* s, photon_t* p) {
   const orc_phantom* ph = X->ph;
@@ -415,7 +430,7 @@ static void track_photon(const sim_ctx* X, stream_t* s, photon_t* p) {
         memcpy(p->c_dir_before, d0, sizeof d0);
         memcpy(p->c_dir_after, p->dir, sizeof d0);
       }
-      if (p->e < X->sc->e_lo) { p->status = ORC_ENERGY_WINDOW; return; }
+      if (p->e < e_kill(X->sc)) { p->status = ORC_ENERGY_WINDOW; return; }
     } else if (t < mc + mr) {                    /* Rayleigh */
       double c = sample_rayleigh(s, p->e, mt->kappa[m]);
       double phi = 2.0 * PI * next_u(s);
@@ -430,6 +445,12 @@ static void track_photon(const sim_ctx* X, stream_t* s, photon_t* p) {
   int st = orc_detect(X->sc, p->pos, p->dir, p->e, &p->crystal, &p->ring, p->hit, &p->alpha,
                       &p->beta, &dist);
   p->path += dist;
+  p->e_det = p->e;
+  if (X->sc->e_res > 0.0 && st != ORC_LOST_AXIAL) {
+    double u1 = next_u(s), u2 = next_u(s);
+    p->e_det = p->e + e_sigma(X->sc, p->e) * sqrt(-2.0 * log(u1)) * cos(2.0 * PI * u2);
+    st = (p->e_det < X->sc->e_lo || p->e_det > X->sc->e_hi) ? ORC_ENERGY_WINDOW : ORC_DETECTED;
+  }
   p->status = st;
   if (st == ORC_DETECTED)
     p->prob = orc_lut_prob(X->lut, p->e, p->alpha, p->beta, p->crystal % X->sc->module_t,
@@ -477,6 +498,7 @@ static void run_history(const sim_ctx* X, uint64_t h, orc_record* r) {
     r->n_rayleigh[k] = P[k].n_rayleigh;
     r->n_steps[k] = P[k].n_steps;
     r->energy[k] = P[k].e;
+    r->e_det[k] = P[k].e_det;
     r->alpha[k] = P[k].alpha;
     r->beta[k] = P[k].beta;
     r->path[k] = P[k].path;

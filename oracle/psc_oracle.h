@@ -49,6 +49,9 @@ typedef struct {
   int32_t n_rad;       /* radial bins kept (centred clip of the n_crystals-1 bins) */
   double tof_bin_mm;   /* TOF bin width of (l_a - l_b)/2 (mm) */
   double tof_sigma_mm; /* Gaussian blur sigma of (l_a - l_b)/2 (mm); 0 = none */
+  double e_res;        /* energy resolution, FWHM as a fraction of 511 keV at 511 keV, scaling
+                          as sqrt(E); 0 = exact energies.  The window then tests the blurred
+                          energy, and a Compton photon is dropped below e_lo - 5 sigma(e_lo). */
 } orc_scanner;
 
 typedef struct {
@@ -93,6 +96,7 @@ typedef struct {
   double exit_dir[2][3];   /* direction at detection */
   /* first Compton interaction of photon 1 (zeros if none) */
   double c_e_before, c_e_after, c_dir_before[3], c_dir_after[3];
+  double e_det[2];         /* energy the window tested (blurred when e_res > 0) */
 } orc_record;
 
 /* Philox4x32-10 block function (Salmon et al., SC'11). */

@@ -39,7 +39,8 @@ class ScannerDesc(C.Structure):
     _fields_ = [("radius", C.c_double), ("ring_pitch", C.c_double), ("n_crystals", C.c_int32),
                 ("n_rings", C.c_int32), ("module_t", C.c_int32), ("module_a", C.c_int32),
                 ("e_lo", C.c_double), ("e_hi", C.c_double), ("n_tof", C.c_int32),
-                ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double)]
+                ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double),
+                ("e_res_fwhm", C.c_double)]
 
 
 class MaterialsDesc(C.Structure):
@@ -365,7 +366,7 @@ class _Held:
 def scanner_desc(sc):
     return ScannerDesc(sc.radius, sc.ring_pitch, sc.n_crystals, sc.n_rings, sc.module_t,
                        sc.module_a, sc.e_lo, sc.e_hi, sc.n_tof, sc.n_rad, sc.tof_bin_mm,
-                       sc.tof_sigma_mm)
+                       sc.tof_sigma_mm, getattr(sc, "e_res", 0.0))
 
 
 def materials_desc(mats):

@@ -37,6 +37,8 @@ enum : int {
 struct ScannerParams {
   float radius, r2, half_len, inv_pitch;
   float e_lo, e_hi;
+  float e_res_k;               // energy resolution: sigma(E) = e_res_k sqrt(E) (keV); 0 = exact
+  float e_kill;                // a Compton photon below this energy cannot be detected
   float crystals_per_radian;   // N / (2 pi)
   float inv_tof_bin, tof_half, tof_sigma;
   int n_crystals, n_rings, module_t, module_a, n_tof, n_rad, n_views, rad_off;

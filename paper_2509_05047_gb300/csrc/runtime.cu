@@ -280,6 +280,7 @@ int check_scanner(const psc_scanner_desc* d) {
     return fail(PSC_EINVAL, "radius, ring_pitch, tof_bin_mm must be > 0 and tof_sigma_mm >= 0");
   if (d->module_t < 1 || d->module_a < 1) return fail(PSC_EINVAL, "module sizes must be >= 1");
   if (!(d->e_hi >= d->e_lo) || !(d->e_lo >= 0)) return fail(PSC_EINVAL, "bad energy window");
+  if (!(d->e_res_fwhm >= 0.0 && d->e_res_fwhm < 1.0)) return fail(PSC_EINVAL, "e_res_fwhm must be in [0, 1)");
   return PSC_OK;
 }
 
@@ -376,6 +377,13 @@ int psc_load_scanner(psc_ctx* ctx, const psc_scanner_desc* d, int32_t* id) {
   s.inv_pitch = (float)(1.0 / d->ring_pitch);
   s.e_lo = (float)d->e_lo;
   s.e_hi = (float)d->e_hi;
+  // FWHM e_res * 511 keV at 511 keV, scaling as sqrt(E); photons more than
+  // 5 sigma below the window after a Compton event are dropped
+  const double fwhm_to_sigma = 2.0 * std::sqrt(2.0 * std::log(2.0));
+  s.e_res_k = (float)(d->e_res_fwhm * std::sqrt(511.0) / fwhm_to_sigma);
+  s.e_kill = d->e_res_fwhm > 0.0
+                 ? (float)std::max(0.0, d->e_lo - 5.0 * d->e_res_fwhm * std::sqrt(511.0 * d->e_lo) / fwhm_to_sigma)
+                 : (float)d->e_lo;
   s.crystals_per_radian = (float)(d->n_crystals / (2.0 * M_PI));
   s.inv_tof_bin = (float)(1.0 / d->tof_bin_mm);
   s.tof_half = (float)(0.5 * d->n_tof);
@@ -727,7 +735,8 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   q.nz = pd.nz;
   q.n_mat = ph->n_mat;
   q.n_e = ph->n_e;
-  q.e0 = std::max(0, std::min((int)std::floor(sc->desc.e_lo) - 1, ph->n_e - 2));
+  // staged table nodes: from just below the lowest energy a tracked photon can have
+  q.e0 = std::max(0, std::min((int)std::floor(sc->params.e_kill) - 1, ph->n_e - 2));
   q.n_tab = ph->n_e - q.e0;
   q.n_vox = ph->n_vox;
   q.ox = (float)pd.ox;

@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         // ---- refill the slot's window: the single Philox evaluation ----
         uint32_t k = U(F_K, g), nb = U(F_NB, g);
         int need = (int)((kNeedNibbles >> (4 * sec)) & 15u);
+        if (sec == kEscape && S.e_res_k > 0.0f) need = 2;  // Box-Muller pair of the energy blur
         if (sec == kCoinc && !blur) need = 0;
         if (k + need > 4 * nb) {
           const uint32_t hlo = U(F_HLO, g), hhi = U(F_HHI, g), stream = U(F_META, g) >> 4;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             ++k;
             const float e1 = e / x;
             count(true, kStatCompton);
-            if (e1 < S.e_lo) {
+            if (e1 < S.e_kill) {
               finish(g, kEnergyWindow, -1, 0);
             } else {
               setF(F_DX, g, d.x);
@@ -474,7 +475,12 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
               cr = max(0, min((int)floorf(phi * S.crystals_per_radian), S.n_crystals - 1));
               nx = hx / S.radius;
               ny = hy / S.radius;
-              if (e < S.e_lo || e > S.e_hi) cls = kEnergyWindow;
+              float ed = e;  // the energy the window tests: blurred by the resolution, if any
+              if (S.e_res_k > 0.0f) {
+                ed = e + S.e_res_k * sqrtf(e) * (sqrtf(-2.0f * __logf(uni(k))) * cospif(2.0f * uni(k + 1)));
+                k += 2;
+              }
+              if (ed < S.e_lo || ed > S.e_hi) cls = kEnergyWindow;
             }
           }
           count(cls == kDetected, kStatDetected);

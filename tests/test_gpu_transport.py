@@ -264,3 +264,31 @@ def test_alias_table_equals_oracle(tiny):
         k = np.clip(k, 0, (1 << 23) - 1)
         np.testing.assert_array_equal(k < thr, (2 * k + 1) * 2.0**-24 < prob)
     psc.psc_update_activity(tiny.ctx, tiny.p_id, tiny.ph.activity)
+
+
+def test_energy_resolution_variant_matches_oracle():
+    """No-LUT mode of Sec. 2.2.1: 11.2 % energy resolution and a 425-650 keV
+    window.  The blurred energy decides the window on both sides from the
+    same two words of the photon's stream, so histories match as without
+    resolution; some photons below 425 keV are detected."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_tiny()
+    sc.e_res = 0.112
+    mats, ph = W.standard_materials(), W.phantom_water_cylinder()
+    s = Session(sc, mats, ph, None)
+    try:
+        n = 200_000
+        g = s.run(SEED + 21, 0, n, lut=0)
+        r = oracle.simulate(sc, mats, ph, None, SEED + 21, 0, n, threads=8, records=True)
+        same = compare_histories(g, r)
+        assert (~same).sum() <= 0.001 * n
+        rec = r["rec"]
+        det = rec["status"] == oracle.DETECTED
+        assert np.any(det & (rec["energy"] < sc.e_lo))
+        # the window's decisions differ from those on exact energies at the same seed
+        exact = oracle.simulate(W.scanner_tiny(), mats, ph, None, SEED + 21, 0, n, threads=8)
+        assert (g["cls"] == oracle.ENERGY_WINDOW).sum() != (exact["cls"] == oracle.ENERGY_WINDOW).sum()
+    finally:
+        s.close()

@@ -120,6 +120,7 @@ class Scanner:
     tof_bin_mm: float      # TOF bin width in half-path-difference units (mm)
     tof_sigma_mm: float    # Gaussian TOF blur sigma (mm), 0 = none
     n_rad: int = 0         # radial bins kept (centred clip); 0 -> n_crystals - 1
+    e_res: float = 0.0     # energy resolution FWHM / 511 keV at 511 keV (scaling as sqrt(E)); 0 = exact
 
     def __post_init__(self):
         if self.n_rad == 0:
