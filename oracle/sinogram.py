@@ -173,3 +173,72 @@ def finalize_at(bins, shape, n_rings, acc_at, sens_at=None, norm_at=None, sigma=
     if smooth_before_sensitivity and sens_at is not None:
         x = x * sens_at(bins)
     return x
+
+
+# ---------------------------------------------------------------------------
+# Post-processing beyond the estimate (Sec. 2.2.4, 2.3.2, 4)
+# ---------------------------------------------------------------------------
+def mash(s, view_factor=1, tof_factor=1):
+    """Mashing (Sec. 4 lists it as a way to need fewer counts): adjacent
+    views and adjacent TOF bins are summed, [p][v][r][t] ->
+    [p][v / view_factor][r][t / tof_factor]."""
+    p, v, r, t = s.shape
+    if v % view_factor or t % tof_factor:
+        raise ValueError("factors must divide the view and TOF counts")
+    return s.reshape(p, v // view_factor, view_factor, r, t // tof_factor, tof_factor).sum(axis=(2, 5))
+
+
+def _view_rad(n, a, b, rad_off):
+    """View and kept-radial index of the LOR between crystals a < b (the
+    integer LOR formula of the binning)."""
+    f = a + b
+    s = np.where(f >= n, -1, 1)
+    f = np.where(f >= n, f - n, f)
+    return f >> 1, s * (n // 2 - (b - a)) + n // 2 - 1 - rad_off
+
+
+def rotational_average(s, n_crystals, n_rings, step):
+    """Average over the scanner's rotational symmetries (Sec. 2.2.4 exploits
+    14 of them for the sensitivity sinograms).  Rotating the ring by a whole
+    module of `step` crystals maps it onto itself; the n / step rotations
+    form a group whose orbit of an LOR visits n / (2 step) views of a
+    180-degree sinogram (14 for 448 crystals in 16-crystal modules), each
+    twice: the half turn maps a bin to its radial mirror.  Rotation by c
+    crystals maps the LOR (a, b, ring_a, ring_b, delta) to (a + c, b + c)
+    mod n; when that reverses the crystal order, the rings swap roles and the
+    TOF coordinate changes sign (bin t -> n_tof - 1 - t).  Brute force over
+    every crystal pair with the forward LOR formula."""
+    if n_crystals % step:
+        raise ValueError("step must divide n_crystals")
+    n_rot = n_crystals // step
+    n, nr = n_crystals, n_rings
+    p_, v_, r_, t_ = s.shape
+    rad_off = (n - 1 - r_) // 2
+    a, b = np.triu_indices(n, 1)
+    v0, r0 = _view_rad(n, a, b, rad_off)
+    keep = (r0 >= 0) & (r0 < r_)
+    a, b, v0, r0 = a[keep], b[keep], v0[keep], r0[keep]
+    ra, rb = np.divmod(np.arange(p_), nr)
+    swapped = rb * nr + ra
+    out = np.zeros_like(s, dtype=np.float64)
+    for k in range(n_rot):
+        c = k * step
+        a2, b2 = (a + c) % n, (b + c) % n
+        flip = a2 > b2
+        lo, hi = np.minimum(a2, b2), np.maximum(a2, b2)
+        v2, r2 = _view_rad(n, lo, hi, rad_off)
+        if np.any((r2 < 0) | (r2 >= r_)):
+            raise ValueError("a rotation leaves the kept radial range")
+        for fl in (False, True):
+            m = flip == fl
+            src = s[swapped][:, v2[m], r2[m], ::-1] if fl else s[:, v2[m], r2[m], :]
+            out[:, v0[m], r0[m], :] += src
+    return out / n_rot
+
+
+def norm_from_sinogram(s, n_rings, sigma):
+    """Smoothing-normalisation sinogram (Sec. 2.3.2): a heavily smoothed
+    copy of a sinogram divided by the sinogram itself; 0 where it is 0."""
+    sm = smooth(s.astype(np.float64), n_rings, sigma)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(s != 0, sm / np.where(s != 0, s, 1.0), 0.0)
