@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--histories", type=float, default=1e9)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "precision", "batched", "served"],
+    ap.add_argument("--mode", default="step", choices=["step", "precision", "batched", "served", "postproc"],
                     help="step: the benchmark line; precision: LUT precision / count-level study; "
                          "batched / served: request server vs plain sequential requests")
     ap.add_argument("--requests", type=int, default=32, help="batched: phantoms; served: chains")
@@ -608,8 +608,58 @@ def run_requests(a):
             "note": "served results are bit-identical to the same requests alone (tests/test_gpu_server.py)"}
 
 
+# ---------------------------------------------------------------------------
+# post-processing calls on the paper-scale sinogram
+# ---------------------------------------------------------------------------
+def run_postproc(a):
+    import torch
+    import paper_2509_05047_gb300 as psc
+    from paper_2509_05047_gb300 import build as B
+    B.build()
+    sc = W.scanner_signa()
+    ctx = psc.psc_create(0)
+    s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
+    a_id, o_id = psc.psc_acc_create(ctx, s_id), psc.psc_acc_create(ctx, s_id)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    # a dense synthetic accumulator (every bin non-zero, as after a long run)
+    acc = torch.empty(sc.n_bins, dtype=torch.int64, device="cuda")
+    acc.random_(1 << 20, 1 << 36, generator=torch.Generator(device="cuda").manual_seed(1))
+    psc.psc_acc_write(ctx, a_id, acc, sh)
+    del acc
+    out = torch.empty(sc.shape, dtype=torch.float64, device="cuda")
+    mashed = torch.empty((sc.n_planes, sc.n_views // 2, sc.n_rad, sc.n_tof), dtype=torch.int64, device="cuda")
+    ops = {
+        "rotate_sum_step16": (lambda: psc.psc_acc_rotate_sum(ctx, a_id, 16, o_id, sh), 16),
+        "mash_views2": (lambda: psc.psc_acc_mash(ctx, a_id, 2, 1, mashed, sh), 12),
+        "norm_sinogram_sigma4": (lambda: psc.psc_norm_sinogram(ctx, a_id, (4.0, 4.0, 4.0), out, sh), 32),
+    }
+    peaks, src = measured_peaks()
+    res = {"mode": "postproc", "workload": "paper-scale sinogram 2025x224x447x27 (5.47e9 bins), dense int64",
+           "hbm_peak_gbs": peaks["hbm_gbs"], "ops": {}}
+    for name, (f, bytes_per_bin) in ops.items():
+        for _ in range(2):
+            f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        gbs = bytes_per_bin * sc.n_bins / (ms / 1e3) / 1e9
+        res["ops"][name] = {"ms": round(ms, 3), "algorithmic_bytes_per_bin": bytes_per_bin,
+                            "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 3)}
+    psc.psc_destroy(ctx)
+    return res
+
+
 def main():
     a = parse()
+    if a.mode == "postproc":
+        print(json.dumps(run_postproc(a)))
+        return
     if a.mode in ("batched", "served"):
         print(json.dumps(run_requests(a)))
         return

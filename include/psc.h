@@ -218,6 +218,33 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
  * and (2 n_rings - 1) * n_crystals / 2 <= 65535, else PSC_EINVAL. */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
+/* Smoothing-normalisation sinogram (Sec. 2.3.2: a heavily smoothed copy of
+ * a sinogram divided by the sinogram itself, made once from the simulation
+ * of a large cylinder): out[bin] = smooth(acc)[bin] / acc[bin], 0 where
+ * acc[bin] == 0; sigma (host [3], bins: radial, view, axial) as in
+ * psc_finalize_args.  out: device f64 of the scanner's sinogram size, used
+ * as working memory until the last pass writes it.  The ratio is computed
+ * in FP32 (the smoothed value's precision) and widened exactly.  Load it
+ * with psc_load_sinogram (per bin) to use it as the normalisation. */
+int psc_norm_sinogram(psc_ctx* ctx, int32_t acc, const double* sigma, double* out /* device */,
+                      psc_stream stream);
+/* Mashing (Sec. 4 lists it to need fewer counts and less smoothing): sums
+ * view_factor adjacent views and tof_factor adjacent TOF bins of an
+ * accumulator into out, device int64 [planes][views / view_factor][n_rad]
+ * [n_tof / tof_factor]; the factors must divide the view and TOF counts.
+ * Exact integer sums. */
+int psc_acc_mash(psc_ctx* ctx, int32_t acc, int32_t view_factor, int32_t tof_factor,
+                 int64_t* out /* device */, psc_stream stream);
+/* Sum over the scanner's rotational symmetries (Sec. 2.2.4 averages the
+ * sensitivity sinograms over 14 of them): out_acc = sum over the
+ * n_crystals / step rotations by k * step crystals (step = crystals per
+ * module) of acc at the rotated LOR; when a rotation reverses the crystal
+ * order the rings swap and the TOF bin mirrors.  The orbit of an LOR visits
+ * n_crystals / (2 step) views (14 for 448 crystals in modules of 16), each
+ * twice.  Exact integer sums; the average is this sum with finalize scale
+ * 1 / (n_crystals / step).  out_acc: another accumulator of the same
+ * scanner; at most 255 rings. */
+int psc_acc_rotate_sum(psc_ctx* ctx, int32_t acc, int32_t step, int32_t out_acc, psc_stream stream);
 /* Allocation-free variant of psc_finalize for callers that cannot allocate
  * device memory (their device memory belongs to another allocator, is
  * capped, or must not be allocated once a real-time loop is running).  The

@@ -197,7 +197,7 @@ def _view_rad(n, a, b, rad_off):
     return f >> 1, s * (n // 2 - (b - a)) + n // 2 - 1 - rad_off
 
 
-def rotational_average(s, n_crystals, n_rings, step):
+def rotational_average(s, n_crystals, n_rings, step, average=True):
     """Average over the scanner's rotational symmetries (Sec. 2.2.4 exploits
     14 of them for the sensitivity sinograms).  Rotating the ring by a whole
     module of `step` crystals maps it onto itself; the n / step rotations
@@ -207,7 +207,8 @@ def rotational_average(s, n_crystals, n_rings, step):
     crystals maps the LOR (a, b, ring_a, ring_b, delta) to (a + c, b + c)
     mod n; when that reverses the crystal order, the rings swap roles and the
     TOF coordinate changes sign (bin t -> n_tof - 1 - t).  Brute force over
-    every crystal pair with the forward LOR formula."""
+    every crystal pair with the forward LOR formula.  average=False returns
+    the sum over the rotations (exact for an int64 fixed-point sinogram)."""
     if n_crystals % step:
         raise ValueError("step must divide n_crystals")
     n_rot = n_crystals // step
@@ -220,7 +221,7 @@ def rotational_average(s, n_crystals, n_rings, step):
     a, b, v0, r0 = a[keep], b[keep], v0[keep], r0[keep]
     ra, rb = np.divmod(np.arange(p_), nr)
     swapped = rb * nr + ra
-    out = np.zeros_like(s, dtype=np.float64)
+    out = np.zeros(s.shape, dtype=np.int64 if (s.dtype.kind == "i" and not average) else np.float64)
     for k in range(n_rot):
         c = k * step
         a2, b2 = (a + c) % n, (b + c) % n
@@ -233,7 +234,7 @@ def rotational_average(s, n_crystals, n_rings, step):
             m = flip == fl
             src = s[swapped][:, v2[m], r2[m], ::-1] if fl else s[:, v2[m], r2[m], :]
             out[:, v0[m], r0[m], :] += src
-    return out / n_rot
+    return out / n_rot if average else out
 
 
 def norm_from_sinogram(s, n_rings, sigma):

@@ -133,6 +133,9 @@ SIGNATURES = {
     "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
     "psc_finalize_static": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _I32, _P,
                                       C.c_double, _I32, _P, _P]),
+    "psc_norm_sinogram": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "psc_acc_mash": (C.c_int, [_P, _I32, _I32, _I32, _P, _P]),
+    "psc_acc_rotate_sum": (C.c_int, [_P, _I32, _I32, _I32, _P]),
     "psc_unload": (C.c_int, [_P, _I32]),
     "psc_resident_bytes": (_U64, [_P]),
     "psc_phantom_voxels": (C.c_int64, [_P, _I32]),
@@ -291,6 +294,22 @@ def psc_finalize_static(acc, n_rings, n_crystals, n_rad, n_tof, out, sens=None, 
     _check(lib().psc_finalize_static(_ptr(acc), n_rings, n_crystals, n_rad, n_tof, _ptr(sens),
                                      1 if sens_per_lor else 0, _ptr(norm), 1 if norm_per_lor else 0,
                                      sig, scale, 1 if sens_first else 0, _ptr(out), _stream(stream)))
+
+
+def psc_norm_sinogram(ctx, acc, sigma, out, stream=None):
+    """Smoothing-normalisation sinogram smooth(acc) / acc into ``out``."""
+    sig = (C.c_double * 3)(*sigma)
+    _check(lib().psc_norm_sinogram(ctx, acc, sig, _ptr(out), _stream(stream)))
+
+
+def psc_acc_mash(ctx, acc, view_factor, tof_factor, out, stream=None):
+    """Sum adjacent views / TOF bins of an accumulator into ``out`` (int64)."""
+    _check(lib().psc_acc_mash(ctx, acc, view_factor, tof_factor, _ptr(out), _stream(stream)))
+
+
+def psc_acc_rotate_sum(ctx, acc, step, out_acc, stream=None):
+    """Sum of an accumulator over the scanner's module rotations into ``out_acc``."""
+    _check(lib().psc_acc_rotate_sum(ctx, acc, step, out_acc, _stream(stream)))
 
 
 def psc_unload(ctx, obj):

@@ -326,7 +326,9 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // grid (ceil(R T / 256), segments x V); a thread owns the column (segment,
 // view, rad, tof) and slides along the segment's planes p0 + k (n_rings + 1).
 // ---------------------------------------------------------------------------
-template <int KT>
+// kDivide: the output is the smoothed value over the (scaled) input bin,
+// 0 where the input is 0 (the smoothing-normalisation sinogram)
+template <int KT, bool kDivide>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
@@ -348,22 +350,32 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
   // the smoothed value carries FP32 precision: the factors are FP32 (rounded
   // once), multiplied in FP32 and the result widened exactly to FP64.  The
   // factor loads of a step are issued before any output is stored.
+  const float cf = (float)P.c;
   auto store = [&](int k0, const float (&o)[NB]) {
     const long long b0 = bin0 + k0 * bin_step, l0 = lor0 + k0 * lor_step;
     float fr[NB], fs[NB];
+    long long qa[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const long long bin = b0 + q * bin_step, lor = l0 + q * lor_step;
       const bool in = k0 + q < L;
-      fr[q] = use_rnorm && in ? factor(P.rnorm32, P.rnorm, P.norm_per_lor ? lor : bin) : 1.0f;
-      fs[q] = use_sens && in ? factor(P.sens32, P.sens, P.sens_per_lor ? lor : bin) : 1.0f;
+      if (kDivide) {
+        qa[q] = in ? __ldg(P.acc + bin) : 0;
+      } else {
+        fr[q] = use_rnorm && in ? factor(P.rnorm32, P.rnorm, P.norm_per_lor ? lor : bin) : 1.0f;
+        fs[q] = use_sens && in ? factor(P.sens32, P.sens, P.sens_per_lor ? lor : bin) : 1.0f;
+      }
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       if (k0 + q >= L) break;
       float y = o[q];
-      if (use_rnorm) y *= fr[q];
-      if (use_sens) y *= fs[q];
+      if (kDivide) {
+        y = qa[q] != 0 ? y / (i64_to_f32(qa[q]) * cf) : 0.0f;
+      } else {
+        if (use_rnorm) y *= fr[q];
+        if (use_sens) y *= fs[q];
+      }
       P.out[b0 + q * bin_step] = f32_to_f64(y);
     }
   };
@@ -461,7 +473,14 @@ static cudaError_t dispatch_kt(int kt, const FinParams& p, dim3 grid, cudaStream
   };
 PSC_LAUNCHER(RadialL, smooth_radial_kernel)
 PSC_LAUNCHER(ViewL, smooth_view_kernel)
-PSC_LAUNCHER(AxialL, smooth_axial_kernel)
+template <int KT>
+struct AxialL {
+  static cudaError_t run(const FinParams& p, dim3 grid, cudaStream_t s) {
+    if (p.divide_acc) smooth_axial_kernel<KT, true><<<grid, kSmoothThreads, 0, s>>>(p);
+    else smooth_axial_kernel<KT, false><<<grid, kSmoothThreads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
+};
 
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s) {
   cudaError_t e;

@@ -1,0 +1,108 @@
+// postproc.cu -- post-processing of int64 fixed-point sinograms: mashing of
+// views and TOF bins (Sec. 4 names it as a way to need fewer counts and less
+// smoothing time) and the sum over the scanner's rotational symmetries
+// (Sec. 2.2.4 averages the sensitivity sinograms over them).  Both are exact
+// integer sums, so their results do not depend on summation order.
+//
+// Layout of a sinogram: [plane = ring_a * n_rings + ring_b][view][rad][tof],
+// with the integer LOR formula of the binning: for crystals a < b, f = a + b
+// (f -= n and s = -1 when f >= n, else s = +1), view = f >> 1, radial
+// s (n/2 - (b - a)) + n/2 - 1 less the centred clip offset.
+#include "psc_internal.h"
+
+namespace psc {
+
+namespace {
+
+// out[p][v / vf][r][t / tf] = sum of the vf x tf block; grid (ceil(R T2 /
+// 256), V2, planes)
+__global__ void mash_kernel(const long long* __restrict__ in, long long* __restrict__ out, int V, int R, int T,
+                            int vf, int tf) {
+  const int V2 = V / vf, T2 = T / tf;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R * T2) return;
+  const int r = c / T2, t2 = c - r * T2;
+  const long long p = blockIdx.z;
+  const int v2 = blockIdx.y;
+  long long sum = 0;
+  for (int j = 0; j < vf; ++j) {
+    const long long* row = in + ((p * V + (long long)v2 * vf + j) * R + r) * T + (long long)t2 * tf;
+    for (int u = 0; u < tf; ++u) sum += __ldg(row + u);
+  }
+  out[((p * V2 + v2) * R + r) * T2 + t2] = sum;
+}
+
+// the crystal pair a < b of (view, unclipped radial index): the inverse of
+// the binning's LOR formula (one of s = +1, -1 gives a valid pair)
+__device__ __forceinline__ void lor_crystals(int n, int v, int r_full, int& a, int& b) {
+  const int q = r_full - n / 2 + 1;
+  a = b = -1;
+#pragma unroll
+  for (int si = 0; si < 2; ++si) {
+    const int s = si ? -1 : 1;
+    const int d = n / 2 - s * q;
+    if (d < 1 || d > n - 1) continue;
+    const int f = 2 * v + (d & 1) + (s < 0 ? n : 0);  // a + b
+    const int a2 = f - d;
+    if (a2 < 0 || (a2 & 1)) continue;
+    const int lo = a2 >> 1, hi = (f + d) >> 1;
+    if (lo < hi && hi < n && a < 0) {
+      a = lo;
+      b = hi;
+    }
+  }
+}
+
+// out[bin] = sum over the n / step rotations by k * step crystals of in at
+// the rotated LOR: (a + c, b + c) mod n; when the order reverses, the ring
+// indices swap and the TOF bin mirrors.  grid (ceil(R T / 256), V, planes)
+__global__ void rotate_sum_kernel(const long long* __restrict__ in, long long* __restrict__ out, int n,
+                                  int n_rings, int R, int T, int step) {
+  const int V = n / 2;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R * T) return;
+  const int r = c / T, t = c - r * T;
+  const int v = blockIdx.y;
+  const int p = blockIdx.z;
+  const int ra = p / n_rings, rb = p - ra * n_rings;
+  const int rad_off = (n - 1 - R) / 2;
+  int a, b;
+  lor_crystals(n, v, r + rad_off, a, b);
+  long long sum = 0;
+  int a2 = a, b2 = b;  // (a + k step, b + k step) mod n, kept below n by one subtraction
+  for (int k = 0; k < n / step; ++k, a2 += step, b2 += step) {
+    if (a2 >= n) a2 -= n;
+    if (b2 >= n) b2 -= n;
+    const bool flip = a2 > b2;
+    const int lo = flip ? b2 : a2, hi = flip ? a2 : b2;
+    int f = lo + hi, s = 1;
+    if (f >= n) {
+      f -= n;
+      s = -1;
+    }
+    const int v2 = f >> 1;
+    const int r2 = s * (n / 2 - (hi - lo)) + n / 2 - 1 - rad_off;
+    const long long p2 = flip ? (long long)rb * n_rings + ra : p;
+    const int t2 = flip ? T - 1 - t : t;
+    sum += __ldg(in + ((p2 * V + v2) * R + r2) * T + t2);
+  }
+  out[(((long long)p * V + v) * R + r) * T + t] = sum;
+}
+
+}  // namespace
+
+cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
+                        cudaStream_t s) {
+  const int cols = R * (T / tf);
+  mash_kernel<<<dim3((cols + 255) / 256, V / vf, planes), 256, 0, s>>>(in, out, V, R, T, vf, tf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_sum(const long long* in, long long* out, int n_crystals, int n_rings, int R, int T,
+                              int step, cudaStream_t s) {
+  rotate_sum_kernel<<<dim3((R * T + 255) / 256, n_crystals / 2, n_rings * n_rings), 256, 0, s>>>(
+      in, out, n_crystals, n_rings, R, T, step);
+  return cudaGetLastError();
+}
+
+}  // namespace psc

@@ -28,6 +28,7 @@ struct FinParams {
   long long n_bins;
   int n_rings, V, R, T;
   int smooth, sens_first;
+  int divide_acc;              // output smoothed / (acc * c), 0 where acc == 0 (normalisation sinogram)
   unsigned magic_T;            // ceil(2^32 / T) for exact i / T, 0 when T == 1
   int K[3];                    // truncation radius per axis (radial, view, axial)
   int KT[3];                   // instantiated window radius >= K, or -1: per-tap loop
@@ -54,6 +55,11 @@ cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* bloc
 // or an error code with the message set
 int finalize_plan(FinParams& p, const double sigma[3]);
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s);
+// sinogram post-processing of int64 accumulators (postproc.cu)
+cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
+                        cudaStream_t s);
+cudaError_t launch_rotate_sum(const long long* in, long long* out, int n_crystals, int n_rings, int R, int T,
+                              int step, cudaStream_t s);
 // 1/a (0 where a == 0) into r (FP64) and/or r32 (FP32), either may be nullptr
 cudaError_t launch_reciprocal(const double* a, double* r, float* r32, long long n, int sms, cudaStream_t s);
 // FP32 copy of a sinogram, round to nearest even

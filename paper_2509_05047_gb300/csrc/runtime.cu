@@ -890,7 +890,7 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stre
   return psc_simulate_batch(ctx, a, 1, stats, stream);
 }
 
-int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream) {
+static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide) {
   if (!ctx || !a || !out) return fail(PSC_EINVAL, "NULL argument");
   GET(AccObj, acc, a->acc, kAccObj);
   GET(ScannerObj, sc, acc->scanner, kScannerObj);
@@ -924,6 +924,7 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
   p.T = d.n_tof;
   p.smooth = a->smooth ? 1 : 0;
   p.sens_first = a->sens_first ? 1 : 0;
+  p.divide_acc = divide;
   p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
   if ((long long)p.V * p.R * p.T * p.T >= (1LL << 32))
     return fail(PSC_EOVERFLOW, "a sinogram plane is too large");
@@ -972,6 +973,55 @@ int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stre
     CK(launch_finalize(p, ctx->sms, s), "finalize");
     CK(cudaEventRecord(ctx->scratch_done, s), "order scratch users");
   }
+  return PSC_OK;
+}
+
+int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream) {
+  return finalize_impl(ctx, a, out, stream, 0);
+}
+
+int psc_norm_sinogram(psc_ctx* ctx, int32_t acc, const double* sigma, double* out, psc_stream stream) {
+  if (!sigma) return fail(PSC_EINVAL, "sigma is NULL: the normalisation sinogram is a smoothed ratio");
+  psc_finalize_args a;
+  std::memset(&a, 0, sizeof a);
+  a.acc = acc;
+  a.smooth = 1;
+  for (int i = 0; i < 3; ++i) a.sigma[i] = sigma[i];
+  a.scale = 1.0;
+  return finalize_impl(ctx, &a, out, stream, 1);
+}
+
+int psc_acc_mash(psc_ctx* ctx, int32_t acc, int32_t view_factor, int32_t tof_factor, int64_t* out,
+                 psc_stream stream) {
+  if (!ctx || !out) return fail(PSC_EINVAL, "NULL argument");
+  GET(AccObj, a, acc, kAccObj);
+  GET(ScannerObj, sc, a->scanner, kScannerObj);
+  const psc_scanner_desc& d = sc->desc;
+  const int V = d.n_crystals / 2;
+  if (view_factor < 1 || tof_factor < 1 || V % view_factor || d.n_tof % tof_factor)
+    return fail(PSC_EINVAL, "mashing factors (%d, %d) must divide %d views and %d TOF bins", view_factor, tof_factor,
+                V, d.n_tof);
+  DeviceGuard g(ctx->device);
+  CK(launch_mash((const long long*)a->data.p, (long long*)out, d.n_rings * d.n_rings, V, d.n_rad, d.n_tof,
+                 view_factor, tof_factor, (cudaStream_t)stream),
+     "mash");
+  return PSC_OK;
+}
+
+int psc_acc_rotate_sum(psc_ctx* ctx, int32_t acc, int32_t step, int32_t out_acc, psc_stream stream) {
+  if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
+  GET(AccObj, a, acc, kAccObj);
+  GET(AccObj, o, out_acc, kAccObj);
+  GET(ScannerObj, sc, a->scanner, kScannerObj);
+  if (acc == out_acc) return fail(PSC_EINVAL, "the rotation sum needs a separate output accumulator");
+  if (o->scanner != a->scanner) return fail(PSC_EINVAL, "output accumulator belongs to another scanner");
+  const psc_scanner_desc& d = sc->desc;
+  if (step < 1 || d.n_crystals % step) return fail(PSC_EINVAL, "step %d must divide %d crystals", step, d.n_crystals);
+  if (d.n_rings > 255) return fail(PSC_EINVAL, "at most 255 rings");
+  DeviceGuard g(ctx->device);
+  CK(launch_rotate_sum((const long long*)a->data.p, (long long*)o->data.p, d.n_crystals, d.n_rings, d.n_rad,
+                       d.n_tof, step, (cudaStream_t)stream),
+     "rotation sum");
   return PSC_OK;
 }
 
