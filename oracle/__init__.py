@@ -51,7 +51,9 @@ class Scanner(C.Structure):
                 ("n_rings", C.c_int32), ("module_t", C.c_int32), ("module_a", C.c_int32),
                 ("e_lo", C.c_double), ("e_hi", C.c_double), ("n_tof", C.c_int32),
                 ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double),
-                ("e_res", C.c_double)]
+                ("e_res", C.c_double), ("gap_mode", C.c_int32), ("gap_t", C.c_double),
+                ("gap_a", C.c_double), ("crystal_depth", C.c_double), ("doi", C.c_double),
+                ("mu_block", C.c_double)]
 
 
 class Materials(C.Structure):
@@ -139,6 +141,10 @@ def lib():
         L.orc_bin.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
                               P, P, P, P, P]
         L.orc_bin.restype = C.c_int
+        L.orc_place.argtypes = [P, P, P, P, P, P, P, P, P, P]
+        L.orc_place.restype = C.c_int
+        L.orc_edge_prob.argtypes = [P, C.c_double, C.c_double, C.c_double]
+        L.orc_edge_prob.restype = C.c_double
         _lib = L
     return _lib
 
@@ -164,7 +170,10 @@ class _Keep:
 def scanner_struct(sc):
     return _Keep(Scanner(sc.radius, sc.ring_pitch, sc.n_crystals, sc.n_rings, sc.module_t,
                          sc.module_a, sc.e_lo, sc.e_hi, sc.n_tof, sc.n_rad, sc.tof_bin_mm,
-                         sc.tof_sigma_mm, getattr(sc, "e_res", 0.0)))
+                         sc.tof_sigma_mm, getattr(sc, "e_res", 0.0), getattr(sc, "gap_mode", 0),
+                         getattr(sc, "gap_t", 0.0), getattr(sc, "gap_a", 0.0),
+                         getattr(sc, "crystal_depth", 25.0), getattr(sc, "doi", 7.0),
+                         getattr(sc, "mu_block", 0.0869)))
 
 
 def materials_struct(mats):
@@ -310,3 +319,22 @@ def bin_lor(scanner, ca, cb, ra, rb, delta):
     st = lib().orc_bin(s.ref(), ca, cb, ra, rb, float(delta), C.byref(pl), C.byref(vw),
                        C.byref(rd), C.byref(tf), C.byref(k))
     return st, pl.value, vw.value, rd.value, tf.value, k.value
+
+
+def place(scanner, hit):
+    """(flags, tpos, apos, crystal, ring, xt, xa, bt, ba) of a detector hit
+    on a scanner with gaps (flags: 1 transaxial gap, 2 axial gap)."""
+    s = scanner_struct(scanner)
+    h = np.ascontiguousarray(hit, dtype=np.float64)
+    ints = [C.c_int32() for _ in range(6)]
+    xt, xa = C.c_double(), C.c_double()
+    tp, ap, cr, rg, bt, ba = ints
+    fl = lib().orc_place(s.ref(), _ptr(h), C.byref(tp), C.byref(ap), C.byref(cr), C.byref(rg),
+                         C.byref(xt), C.byref(xa), C.byref(bt), C.byref(ba))
+    return fl, tp.value, ap.value, cr.value, rg.value, xt.value, xa.value, bt.value, ba.value
+
+
+def edge_prob(scanner, x0, theta_deg, gap):
+    """Probability of assignment to the negative-offset block of a gap."""
+    s = scanner_struct(scanner)
+    return lib().orc_edge_prob(s.ref(), float(x0), float(theta_deg), float(gap))

@@ -292,6 +292,84 @@ int orc_detect(const orc_scanner* sc, const double p[3], const double d[3], doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gaps between modules and blocks (Sec. 2.2.1-2.2.2)                        */
+/* ------------------------------------------------------------------------ */
+int orc_place(const orc_scanner* sc, const double hit[3], int32_t* tpos, int32_t* apos,
+              int32_t* crystal, int32_t* ring, double* xt, double* xa, int32_t* bt, int32_t* ba) {
+  int mt = sc->module_t, ma = sc->module_a;
+  int n_mod = sc->n_crystals / mt, n_blk = sc->n_rings / ma;
+  double R = sc->radius;
+  /* transaxial: module m spans azimuth [m Phi, (m+1) Phi), half gaps of gamma / 2 at its ends */
+  double Phi = 2.0 * PI / n_mod, gamma = sc->gap_t / R;
+  double phi = atan2(hit[1], hit[0]);
+  if (phi < 0.0) phi += 2.0 * PI;
+  int m = (int)floor(phi / Phi);
+  if (m > n_mod - 1) m = n_mod - 1;
+  double u = phi - m * Phi;
+  int flags = 0;
+  *crystal = -1;
+  *ring = -1;
+  *xt = 0.0;
+  *xa = 0.0;
+  *bt = -1;
+  *ba = -1;
+  if (u < 0.5 * gamma) {
+    *tpos = 0; *bt = m; *xt = u * R; flags |= 1;
+  } else if (u >= Phi - 0.5 * gamma) {
+    *tpos = mt + 1; *bt = m + 1; *xt = (u - Phi) * R; flags |= 1;
+  } else {
+    int j = (int)floor((u - 0.5 * gamma) / ((Phi - gamma) / mt));
+    if (j > mt - 1) j = mt - 1;
+    *tpos = j + 1;
+    *crystal = m * mt + j;
+  }
+  /* axial: block b spans [b P, (b+1) P) from the scanner's lower end, half gaps at its ends */
+  double L = sc->n_rings * sc->ring_pitch, P = L / n_blk, ga = sc->gap_a;
+  double z = hit[2] + 0.5 * L;
+  int b = (int)floor(z / P);
+  if (b > n_blk - 1) b = n_blk - 1;
+  if (b < 0) b = 0;
+  double w = z - b * P;
+  int al;
+  if (w < 0.5 * ga) {
+    al = 0; *ba = b; *xa = w; flags |= 2;
+  } else if (w >= P - 0.5 * ga) {
+    al = ma + 1; *ba = b + 1; *xa = w - P; flags |= 2;
+  } else {
+    int j = (int)floor((w - 0.5 * ga) / ((P - ga) / ma));
+    if (j > ma - 1) j = ma - 1;
+    al = j + 1;
+    *ring = b * ma + j;
+  }
+  *apos = b * (ma + 2) + al;
+  return flags;
+}
+
+double orc_edge_prob(const orc_scanner* sc, double x0, double theta_deg, double gap) {
+  double D = sc->crystal_depth, y0 = sc->doi, mu = sc->mu_block;
+  double th = theta_deg * PI / 180.0;
+  double s = tan(th), c = cos(th);
+  double l1 = 0.0, l2 = 0.0;
+  if (s != 0.0) {
+    /* the line x(y) = x0 + (y - y0) s meets x = -gap/2 at ya and x = +gap/2 at yb */
+    double ya = y0 + (-0.5 * gap - x0) / s, yb = y0 + (0.5 * gap - x0) / s;
+    if (s > 0.0) {  /* block 1 at small depth, block 2 at large depth */
+      l1 = fmax(0.0, fmin(D, ya) - 0.0) / c;
+      l2 = fmax(0.0, D - fmax(0.0, yb)) / c;
+    } else {        /* block 2 at small depth, block 1 at large depth */
+      l2 = fmax(0.0, fmin(D, yb) - 0.0) / c;
+      l1 = fmax(0.0, D - fmax(0.0, ya)) / c;
+    }
+  }
+  double first = s > 0.0 ? l1 : l2, second = s > 0.0 ? l2 : l1;
+  double pf = 1.0 - exp(-mu * first);
+  double ps = exp(-mu * first) * (1.0 - exp(-mu * second));
+  double p1 = s > 0.0 ? pf : ps, p2 = s > 0.0 ? ps : pf;
+  if (!(p1 + p2 > 0.0)) return x0 < 0.0 ? 1.0 : (x0 > 0.0 ? 0.0 : 0.5);
+  return p1 / (p1 + p2);
+}
+
+/* ------------------------------------------------------------------------ */
 /* 5D LUT (Sec. 2.2.2): multilinear in (E, alpha, beta) on bin-centre nodes,*/
 /* clamped at the outer nodes; exact in (tpos, apos).                       */
 /* ------------------------------------------------------------------------ */
@@ -452,9 +530,37 @@ static void track_photon(const sim_ctx* X, stream_t* s, photon_t* p) {
     st = (p->e_det < X->sc->e_lo || p->e_det > X->sc->e_hi) ? ORC_ENERGY_WINDOW : ORC_DETECTED;
   }
   p->status = st;
-  if (st == ORC_DETECTED)
-    p->prob = orc_lut_prob(X->lut, p->e, p->alpha, p->beta, p->crystal % X->sc->module_t,
-                           p->ring % X->sc->module_a);
+  if (st != ORC_DETECTED) return;
+  const orc_scanner* sc = X->sc;
+  if (sc->gap_mode == 0) {
+    p->prob = orc_lut_prob(X->lut, p->e, p->alpha, p->beta, p->crystal % sc->module_t,
+                           p->ring % sc->module_a);
+    return;
+  }
+  int32_t tpos, apos, cr, rg, bt, ba;
+  double xt, xa;
+  int flags = orc_place(sc, p->hit, &tpos, &apos, &cr, &rg, &xt, &xa, &bt, &ba);
+  if (flags && sc->gap_mode == 1) { p->status = ORC_LOST_AXIAL; return; }  /* lost in a gap */
+  p->prob = orc_lut_prob(X->lut, p->e, p->alpha, p->beta, tpos, apos);
+  /* a photon in a gap goes to one of the gap's two edge crystals: accept-reject on one
+   * word of its stream against the relative detection probability of the two blocks */
+  int N = sc->n_crystals, cpm = sc->module_t, rpb = sc->module_a, n_blk = sc->n_rings / rpb;
+  if (flags & 1) {
+    double u = next_u(s);
+    double p1 = orc_edge_prob(sc, xt, p->alpha, sc->gap_t);
+    cr = u < p1 ? (bt * cpm - 1 + N) % N : (bt * cpm) % N;
+  }
+  if (flags & 2) {
+    if (ba == 0) rg = 0;                      /* scanner end: one block only */
+    else if (ba == n_blk) rg = sc->n_rings - 1;
+    else {
+      double u = next_u(s);
+      double p1 = orc_edge_prob(sc, xa, p->beta, sc->gap_a);
+      rg = u < p1 ? ba * rpb - 1 : ba * rpb;
+    }
+  }
+  p->crystal = cr;
+  p->ring = rg;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -596,7 +702,12 @@ int orc_simulate(const orc_scanner* sc, const orc_materials* mat, const orc_phan
                  int8_t* cls, int64_t* key, int64_t* q, double* w, orc_record* rec,
                  int64_t* acc, uint64_t* counts) {
   if (check_inputs(sc, mat, ph) != 0 || !alias_prob || !alias_idx) return -1;
-  if (lut && lut->data && (lut->n_tpos != sc->module_t || lut->n_apos != sc->module_a)) return -1;
+  if (sc->gap_mode != 0 && (sc->n_crystals % sc->module_t || sc->n_rings % sc->module_a)) return -1;
+  if (lut && lut->data) {
+    int nt = sc->gap_mode ? sc->module_t + 2 : sc->module_t;
+    int na = sc->gap_mode ? (sc->n_rings / sc->module_a) * (sc->module_a + 2) : sc->module_a;
+    if (lut->n_tpos != nt || lut->n_apos != na) return -1;
+  }
   if (n == 0) return 0;
   sim_ctx X = {sc, mat, ph, alias_prob, alias_idx, lut, NULL, seed, bin_mask};
   X.maj = (double*)malloc(sizeof(double) * (size_t)mat->n_e);

@@ -52,6 +52,21 @@ typedef struct {
   double e_res;        /* energy resolution, FWHM as a fraction of 511 keV at 511 keV, scaling
                           as sqrt(E); 0 = exact energies.  The window then tests the blurred
                           energy, and a Compton photon is dropped below e_lo - 5 sigma(e_lo). */
+  /* Gaps between detector modules (Sec. 2.2.1-2.2.2, Figs. "crystals" and "gap assignment").
+   * gap_mode 0: crystals fill the ring and the axial extent (no gaps).  1 or 2: the ring
+   * holds n_crystals / module_t modules and the axial extent n_rings / module_a blocks;
+   * each module (block) is [half gap | module_t crystals (module_a rings) | half gap], and
+   * LUT positions are the module-local index 0 .. module_t + 1 (0 and module_t + 1: the
+   * virtual crystals of the half gaps) and block * (module_a + 2) + local index 0 ..
+   * module_a + 1.  Mode 1 loses photons in a gap; mode 2 gives them the LUT probability of
+   * their virtual crystal and then assigns them to one of the two edge crystals of the gap
+   * with the relative detection probability of the two blocks (see orc_edge_prob). */
+  int32_t gap_mode;
+  double gap_t;          /* transaxial gap between modules (mm at the detection radius) */
+  double gap_a;          /* axial gap between blocks (mm) */
+  double crystal_depth;  /* crystal length along the radius (mm) */
+  double doi;            /* depth of the detection cylinder below the block face (mm) */
+  double mu_block;       /* attenuation coefficient of the crystals (1/mm) */
 } orc_scanner;
 
 typedef struct {
@@ -128,6 +143,21 @@ double orc_lut_prob(const orc_lut* lut, double e, double alpha, double beta, int
 /* Detection of a photon at pos (inside the cylinder) travelling along dir.
  * Returns ORC_DETECTED or a failure class; fills crystal, ring, hit[3],
  * alpha, beta (deg) and the straight distance to the hit. */
+/* Module / block placement of a detector hit when the scanner has gaps: LUT positions,
+ * crystal and ring (when not in a gap), the signed offset (mm) from the centre of the
+ * transaxial (xt) and axial (xa) gap the hit is in, and the boundary index of that gap
+ * (module bt - 1 | module bt; block ba - 1 | block ba, 0 and n_blocks at the scanner
+ * ends).  Returns 1 for a transaxial gap, 2 for an axial gap, 3 for both, else 0. */
+int orc_place(const orc_scanner* sc, const double hit[3], int32_t* tpos, int32_t* apos,
+              int32_t* crystal, int32_t* ring, double* xt, double* xa, int32_t* bt, int32_t* ba);
+/* Probability that a photon crossing the detection cylinder in a gap, at offset x0 (mm)
+ * from the gap centre with incidence angle theta (deg, positive: the offset grows with
+ * depth), is detected in block 1 (the negative-offset side) rather than block 2: the path
+ * lengths l1, l2 of its line through the two blocks (depth 0 .. crystal_depth, the gap
+ * |x| < gap / 2, the cylinder at depth doi) give the absolute probabilities of the block
+ * met first, p = 1 - exp(-mu l), and of the other, exp(-mu l_first) (1 - exp(-mu l));
+ * the result is p1 / (p1 + p2), or the nearer block when neither block is crossed. */
+double orc_edge_prob(const orc_scanner* sc, double x0, double theta_deg, double gap);
 int orc_detect(const orc_scanner* sc, const double pos[3], const double dir[3], double e,
                int32_t* crystal, int32_t* ring, double hit[3], double* alpha, double* beta,
                double* dist);

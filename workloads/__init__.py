@@ -121,6 +121,12 @@ class Scanner:
     tof_sigma_mm: float    # Gaussian TOF blur sigma (mm), 0 = none
     n_rad: int = 0         # radial bins kept (centred clip); 0 -> n_crystals - 1
     e_res: float = 0.0     # energy resolution FWHM / 511 keV at 511 keV (scaling as sqrt(E)); 0 = exact
+    gap_mode: int = 0      # 0 no gaps; 1 photons in gaps are lost; 2 they go to an edge crystal
+    gap_t: float = 0.0     # transaxial gap between modules (mm at the detection radius)
+    gap_a: float = 0.0     # axial gap between blocks (mm)
+    crystal_depth: float = 25.0   # mm (a project choice: the paper gives no block geometry)
+    doi: float = 7.0       # depth of the detection cylinder below the block face (mm, project choice)
+    mu_block: float = 0.0869      # LYSO attenuation at 511 keV (1/mm)
 
     def __post_init__(self):
         if self.n_rad == 0:
@@ -141,6 +147,16 @@ class Scanner:
     @property
     def shape(self):
         return (self.n_planes, self.n_views, self.n_rad, self.n_tof)
+
+    @property
+    def n_tpos(self):
+        """LUT transaxial positions: module-local crystals (+ 2 virtual with gaps)."""
+        return self.module_t + 2 if self.gap_mode else self.module_t
+
+    @property
+    def n_apos(self):
+        """LUT axial positions: block-local rings, or every block's rings + 2 virtual with gaps."""
+        return (self.n_rings // self.module_a) * (self.module_a + 2) if self.gap_mode else self.module_a
 
     @property
     def n_bins(self):
@@ -174,6 +190,16 @@ def scanner_signa():
     return Scanner(radius=311.8, n_crystals=448, n_rings=45, ring_pitch=250.4 / 45,
                    module_t=16, module_a=9, e_lo=300.0, e_hi=650.0,
                    n_tof=27, tof_bin_mm=24.0, tof_sigma_mm=tof_sigma_from_fwhm_ps(400.0))
+
+
+def scanner_signa_gaps(gap_mode=2, gap_t=2.0, gap_a=2.0):
+    """The paper-scale scanner with gaps between its 28 modules and 5 axial
+    blocks (Sec. 2.2.1-2.2.2; the LUT then has 18 x 55 positions).  The gap
+    widths, crystal depth and depth of interaction are project choices: the
+    paper gives no block geometry."""
+    sc = scanner_signa()
+    sc.gap_mode, sc.gap_t, sc.gap_a = gap_mode, gap_t, gap_a
+    return sc
 
 
 def scanner_small(n_crystals=16, n_rings=4, n_tof=5, radius=120.0, ring_pitch=8.0,
@@ -387,11 +413,11 @@ def lut_smooth(n_e, n_a, n_b, n_tpos, n_apos, e_min, e_max=511.0, seed=3):
 
 
 def lut_tiny(scanner):
-    return lut_smooth(16, 8, 8, scanner.module_t, scanner.module_a, scanner.e_lo)
+    return lut_smooth(16, 8, 8, scanner.n_tpos, scanner.n_apos, scanner.e_lo)
 
 
 def lut_signa(scanner):
-    return lut_smooth(64, 32, 32, scanner.module_t, scanner.module_a, scanner.e_lo)
+    return lut_smooth(64, 32, 32, scanner.n_tpos, scanner.n_apos, scanner.e_lo)
 
 
 # ---------------------------------------------------------------------------
