@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--e-res", type=float, default=0.0,
                     help="energy resolution FWHM at 511 keV (fraction); the no-LUT mode uses 0.112 "
                          "with the small configuration's 425-650 keV window")
+    ap.add_argument("--gaps", type=int, default=0, choices=[0, 1, 2],
+                    help="gaps between modules and blocks: 1 loses photons in a gap, 2 assigns them "
+                         "to edge crystals (paper-scale workload; 2 mm gaps, 18 x 55 LUT positions)")
     ap.add_argument("--precision-workload", default="small", choices=["small", "paper"],
                     help="precision study on the small configuration (water cylinder, 288 x 16 "
                          "scanner) or the paper-scale one")
@@ -153,7 +156,7 @@ def transport_ops(st):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
-def build_inputs(rings=0, tof_bins=0, workload="paper"):
+def build_inputs(rings=0, tof_bins=0, workload="paper", gaps=0):
     if workload == "small":
         sc = W.scanner_tiny()
         return (sc, W.standard_materials(), W.phantom_water_cylinder(), W.lut_tiny(sc),
@@ -165,11 +168,33 @@ def build_inputs(rings=0, tof_bins=0, workload="paper"):
     if tof_bins:
         sc.tof_bin_mm = sc.n_tof * sc.tof_bin_mm / tof_bins
         sc.n_tof = tof_bins
+    if gaps:
+        g = W.scanner_signa_gaps(gap_mode=gaps)
+        sc.gap_mode, sc.gap_t, sc.gap_a = g.gap_mode, g.gap_t, g.gap_a
     mats = W.standard_materials()
     ph = W.phantom_torso()
     lut = W.lut_signa(sc)
     sens = W.sensitivity_uniform(sc.lor_shape, seed=1)
     return sc, mats, ph, lut, sens
+
+
+def workload_inputs(a):
+    """The step workload the options name: inputs and its description."""
+    if a.gaps and a.workload != "paper":
+        raise SystemExit("--gaps applies to the paper-scale workload")
+    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins, a.workload, a.gaps)
+    if a.e_res > 0:
+        sc.e_res = a.e_res
+    base_wl = WORKLOAD_SMALL if a.workload == "small" else WORKLOAD
+    workload = base_wl if not (a.rings or a.tof_bins) else \
+        f"profiling case: {base_wl} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
+    if a.e_res > 0:
+        workload += f", energy resolution {100 * a.e_res:.1f} % FWHM at 511 keV"
+    if a.gaps:
+        workload += (f", {sc.gap_t:g} mm module and {sc.gap_a:g} mm block gaps with LUT positions "
+                     f"{sc.n_tpos}x{sc.n_apos}, "
+                     + ("photons in a gap lost" if a.gaps == 1 else "edge-crystal assignment"))
+    return sc, mats, ph, lut, sens, workload
 
 
 def run_native(a):
@@ -187,9 +212,7 @@ def run_native(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins, a.workload)
-    if a.e_res > 0:
-        sc.e_res = a.e_res
+    sc, mats, ph, lut, sens, workload = workload_inputs(a)
     n = int(a.histories)
     ctx = psc.psc_create(local)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
@@ -298,11 +321,6 @@ def run_native(a):
                          "frac": round(fin_gbs / peaks["hbm_gbs"], 4), "traffic": None,
                          "kernels": "psc::smooth_{radial,view,axial}_kernel", "ms": round(float(phase[2]), 3),
                          "peak_source": f"{src} copy bandwidth"}
-    base_wl = WORKLOAD_SMALL if a.workload == "small" else WORKLOAD
-    workload = base_wl if not (a.rings or a.tof_bins) else \
-        f"profiling case: {base_wl} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
-    if a.e_res > 0:
-        workload += f", energy resolution {100 * a.e_res:.1f} % FWHM at 511 keV"
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -355,10 +373,11 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    sc, mats, ph, lut, sens = build_inputs()
+    import oracle
+    sc, mats, ph, lut, sens, workload = workload_inputs(a)
     n = int(a.histories)
-    for _ in range(a.warmup):
-        pass
+    for i in range(a.warmup):  # untimed: a short oracle run per warm-up step
+        oracle.simulate(sc, mats, ph, lut, 100 + i, 0, 2000, threads=os.cpu_count() or 1)
     vals = []
     t0 = time.perf_counter()
     for _ in range(a.steps):
@@ -370,7 +389,7 @@ def run_reference(a):
             "warmup": a.warmup, "ms_per_step": 1e3 * n / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "histories_per_step": n},
+            "config": {"workload": workload, "histories_per_step": n},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"each step: bounded oracle sample (~8 s) extrapolated to one step; wall {wall:.1f} s"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

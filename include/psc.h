@@ -83,6 +83,22 @@ typedef struct {
                            sqrt(E) (the no-LUT mode of Sec. 2.2.1 uses 0.112 with a 425-650 keV
                            window); 0 = exact energies.  The window tests the blurred energy; a
                            Compton-scattered photon is dropped below e_lo - 5 sigma(e_lo). */
+  /* Gaps between detector modules and blocks (Sec. 2.2.1-2.2.2, Figs. "crystals" and "gap
+   * assignment").  gap_mode 0: crystals fill the ring and the axial extent.  1 or 2: the
+   * ring holds n_crystals / module_t modules and the axial extent n_rings / module_a blocks,
+   * each [half gap | crystals | half gap]; LUT positions are module-local 0 .. module_t + 1
+   * (0 and module_t + 1 are the virtual crystals of the half gaps) and block * (module_a + 2)
+   * + 0 .. module_a + 1.  Mode 1 loses photons in a gap.  Mode 2 gives them the LUT value
+   * of their virtual crystal, then one random word assigns them to one of the gap's two
+   * edge crystals with the relative detection probability of the two blocks: from the path
+   * lengths l1, l2 of the photon's line through the blocks, 1 - exp(-mu l) for the block it
+   * meets first and exp(-mu l_first) (1 - exp(-mu l)) for the other. */
+  int32_t gap_mode;
+  double gap_t_mm;          /* transaxial gap width at the detection radius */
+  double gap_a_mm;          /* axial gap width between blocks */
+  double crystal_depth_mm;  /* crystal length along the radius */
+  double doi_mm;            /* depth of the detection cylinder below the block face */
+  double mu_block;          /* attenuation coefficient of the crystals (1/mm) */
 } psc_scanner_desc;
 
 /* Materials: mass attenuation tables on the grid E = 0, 1, ..., n_e-1 keV

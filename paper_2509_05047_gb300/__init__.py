@@ -40,7 +40,9 @@ class ScannerDesc(C.Structure):
                 ("n_rings", C.c_int32), ("module_t", C.c_int32), ("module_a", C.c_int32),
                 ("e_lo", C.c_double), ("e_hi", C.c_double), ("n_tof", C.c_int32),
                 ("n_rad", C.c_int32), ("tof_bin_mm", C.c_double), ("tof_sigma_mm", C.c_double),
-                ("e_res_fwhm", C.c_double)]
+                ("e_res_fwhm", C.c_double), ("gap_mode", C.c_int32), ("gap_t_mm", C.c_double),
+                ("gap_a_mm", C.c_double), ("crystal_depth_mm", C.c_double), ("doi_mm", C.c_double),
+                ("mu_block", C.c_double)]
 
 
 class MaterialsDesc(C.Structure):
@@ -385,7 +387,10 @@ class _Held:
 def scanner_desc(sc):
     return ScannerDesc(sc.radius, sc.ring_pitch, sc.n_crystals, sc.n_rings, sc.module_t,
                        sc.module_a, sc.e_lo, sc.e_hi, sc.n_tof, sc.n_rad, sc.tof_bin_mm,
-                       sc.tof_sigma_mm, getattr(sc, "e_res", 0.0))
+                       sc.tof_sigma_mm, getattr(sc, "e_res", 0.0), getattr(sc, "gap_mode", 0),
+                       getattr(sc, "gap_t", 0.0), getattr(sc, "gap_a", 0.0),
+                       getattr(sc, "crystal_depth", 25.0), getattr(sc, "doi", 7.0),
+                       getattr(sc, "mu_block", 0.0869))
 
 
 def materials_desc(mats):

@@ -42,6 +42,12 @@ struct ScannerParams {
   float crystals_per_radian;   // N / (2 pi)
   float inv_tof_bin, tof_half, tof_sigma;
   int n_crystals, n_rings, module_t, module_a, n_tof, n_rad, n_views, rad_off;
+  // gaps between modules and blocks (gap_mode 0: none, 1: lost, 2: edge assignment)
+  int gap_mode, n_mod, n_blk;
+  float mod_phi, inv_mod_phi, gap_gamma, inv_crys_phi;  // module pitch, gap (rad), 1 / crystal width
+  float blk_pitch, inv_blk_pitch, gap_a, inv_ring_w;    // block pitch, axial gap (mm), 1 / ring width
+  float gap_t_mm, depth, doi, mu;                       // edge-assignment geometry (mm, 1/mm)
+  int escape_words;  // words of the photon's stream that detection reads: energy blur 2, edge draws 2
 };
 
 struct PhantomParams {

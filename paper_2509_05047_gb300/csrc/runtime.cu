@@ -68,7 +68,7 @@ struct Object {
 
 struct ScannerObj : Object {
   psc_scanner_desc desc;
-  ScannerParams params;
+  ScannerParams params{};
   long long n_bins = 0, n_lor = 0;
   ScannerObj() : Object(kScannerObj) {}
 };
@@ -281,6 +281,17 @@ int check_scanner(const psc_scanner_desc* d) {
   if (d->module_t < 1 || d->module_a < 1) return fail(PSC_EINVAL, "module sizes must be >= 1");
   if (!(d->e_hi >= d->e_lo) || !(d->e_lo >= 0)) return fail(PSC_EINVAL, "bad energy window");
   if (!(d->e_res_fwhm >= 0.0 && d->e_res_fwhm < 1.0)) return fail(PSC_EINVAL, "e_res_fwhm must be in [0, 1)");
+  if (d->gap_mode < 0 || d->gap_mode > 2) return fail(PSC_EINVAL, "gap_mode must be 0, 1 or 2");
+  if (d->gap_mode) {
+    if (d->n_crystals % d->module_t || d->n_rings % d->module_a)
+      return fail(PSC_EINVAL, "with gaps, module_t must divide n_crystals and module_a n_rings");
+    if (!(d->gap_t_mm >= 0) || !(d->gap_a_mm >= 0) || !(d->crystal_depth_mm > 0) || !(d->doi_mm >= 0) ||
+        !(d->mu_block >= 0))
+      return fail(PSC_EINVAL, "gap widths, crystal depth, doi and mu_block must be >= 0 (depth > 0)");
+    if (!(d->gap_t_mm < 2.0 * M_PI * d->radius * d->module_t / d->n_crystals) ||
+        !(d->gap_a_mm < d->n_rings * d->ring_pitch * d->module_a / d->n_rings))
+      return fail(PSC_EINVAL, "a gap must be narrower than its module or block");
+  }
   return PSC_OK;
 }
 
@@ -381,6 +392,25 @@ int psc_load_scanner(psc_ctx* ctx, const psc_scanner_desc* d, int32_t* id) {
   // 5 sigma below the window after a Compton event are dropped
   const double fwhm_to_sigma = 2.0 * std::sqrt(2.0 * std::log(2.0));
   s.e_res_k = (float)(d->e_res_fwhm * std::sqrt(511.0) / fwhm_to_sigma);
+  s.escape_words = (d->e_res_fwhm > 0.0 ? 2 : 0) + (d->gap_mode == 2 ? 2 : 0);
+  s.gap_mode = d->gap_mode;
+  if (d->gap_mode) {
+    s.n_mod = d->n_crystals / d->module_t;
+    s.n_blk = d->n_rings / d->module_a;
+    const double mod_phi = 2.0 * M_PI / s.n_mod, blk_pitch = d->n_rings * d->ring_pitch / s.n_blk;
+    s.mod_phi = (float)mod_phi;
+    s.inv_mod_phi = (float)(1.0 / mod_phi);
+    s.gap_gamma = (float)(d->gap_t_mm / d->radius);
+    s.inv_crys_phi = (float)(d->module_t / (mod_phi - d->gap_t_mm / d->radius));
+    s.blk_pitch = (float)blk_pitch;
+    s.inv_blk_pitch = (float)(1.0 / blk_pitch);
+    s.gap_a = (float)d->gap_a_mm;
+    s.inv_ring_w = (float)(d->module_a / (blk_pitch - d->gap_a_mm));
+    s.gap_t_mm = (float)d->gap_t_mm;
+    s.depth = (float)d->crystal_depth_mm;
+    s.doi = (float)d->doi_mm;
+    s.mu = (float)d->mu_block;
+  }
   s.e_kill = d->e_res_fwhm > 0.0
                  ? (float)std::max(0.0, d->e_lo - 5.0 * d->e_res_fwhm * std::sqrt(511.0 * d->e_lo) / fwhm_to_sigma)
                  : (float)d->e_lo;
@@ -712,9 +742,12 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   if (a->lut != 0) {
     lut = get<LutObj>(ctx, a->lut, kLutObj);
     if (!lut) return fail(PSC_ENOTFOUND, "no lut with id %d", (int)a->lut);
-    if (lut->desc.n_tpos != sc->desc.module_t || lut->desc.n_apos != sc->desc.module_a)
-      return fail(PSC_EINVAL, "LUT positions (%d, %d) do not match scanner modules (%d, %d)",
-                  lut->desc.n_tpos, lut->desc.n_apos, sc->desc.module_t, sc->desc.module_a);
+    const psc_scanner_desc& sd = sc->desc;
+    const int nt = sd.gap_mode ? sd.module_t + 2 : sd.module_t;
+    const int na = sd.gap_mode ? (sd.n_rings / sd.module_a) * (sd.module_a + 2) : sd.module_a;
+    if (lut->desc.n_tpos != nt || lut->desc.n_apos != na)
+      return fail(PSC_EINVAL, "LUT positions (%d, %d) do not match the scanner's (%d, %d)", lut->desc.n_tpos,
+                  lut->desc.n_apos, nt, na);
   }
   if (acc->scanner != a->scanner) return fail(PSC_EINVAL, "accumulator belongs to scanner %d", (int)acc->scanner);
   if (a->first_history + a->n_histories < a->first_history) return fail(PSC_EOVERFLOW, "history range wraps");

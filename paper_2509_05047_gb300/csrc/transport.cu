@@ -55,10 +55,12 @@ enum : int {
   C_E0X, C_E0Y, C_E0Z, C_D0X, C_D0Y, C_D0Z,                 // emission point, photon A direction
   C_ACRG, C_AE, C_APATH, C_ANX, C_ANY, C_ADX, C_ADY, C_ADZ,  // photon A at the detector
   C_BCRG, C_BNX, C_BNY,                                      // photon B at the detector
+  C_APOS, C_BPOS,                                            // LUT positions (scanners with gaps)
   kColdFields
 };
 // F_META = state | photon << 3 | stream << 4;  F_CNT = steps | interactions << 16;
 // C_ACRG = crystal | ring << 16 | scattered << 31;  C_BCRG = crystal | ring << 16;
+// C_APOS, C_BPOS = tpos | apos << 16;
 // F_TRIES = tries (| material << 16 for a pending Rayleigh event)
 __host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
   return (uint32_t)state | (uint32_t)photon << 3 | (uint32_t)stream << 4;
@@ -96,6 +98,102 @@ __device__ __forceinline__ long long bin_key(const ScannerParams& S, int ca, int
   if (!(g >= 0.0f && g < (float)S.n_tof)) return -1;
   const int plane = ra * S.n_rings + rb;
   return (((long long)plane * S.n_views + view) * S.n_rad + r) * S.n_tof + (int)g;
+}
+
+// Gaps between modules and blocks (Sec. 2.2.1-2.2.2).  A photon in a gap
+// goes to the crystal at the gap's low (p) or high (1 - p) edge, p the
+// relative probability that it is absorbed in the block on the low side:
+// its straight line, at slope s = tan(theta) and cos(theta) = c against the
+// radial direction, enters the blocks (depth D, faces doi below the
+// detection cylinder, gap centred at x = 0, the photon at x0) and is
+// absorbed in the first block it crosses with 1 - e^{-mu l1}, in the other
+// with e^{-mu l1} (1 - e^{-mu l2}).  Crossing neither, the nearer side.
+__device__ __forceinline__ float edge_prob(const ScannerParams& S, float x0, float s, float c, float gap) {
+  float l1 = 0.0f, l2 = 0.0f;  // path lengths in the low and high block
+  if (s != 0.0f) {
+    const float ya = S.doi + (-0.5f * gap - x0) / s, yb = S.doi + (0.5f * gap - x0) / s;
+    if (s > 0.0f) {  // the low block is crossed near the face, the high one deeper
+      l1 = fmaxf(0.0f, fminf(S.depth, ya)) / c;
+      l2 = fmaxf(0.0f, S.depth - fmaxf(0.0f, yb)) / c;
+    } else {
+      l2 = fmaxf(0.0f, fminf(S.depth, yb)) / c;
+      l1 = fmaxf(0.0f, S.depth - fmaxf(0.0f, ya)) / c;
+    }
+  }
+  const float first = s > 0.0f ? l1 : l2, second = s > 0.0f ? l2 : l1;
+  const float pf = -expm1f(-S.mu * first);
+  const float ps = expf(-S.mu * first) * -expm1f(-S.mu * second);
+  const float p1 = s > 0.0f ? pf : ps, p2 = s > 0.0f ? ps : pf;
+  if (!(p1 + p2 > 0.0f)) return x0 < 0.0f ? 1.0f : (x0 > 0.0f ? 0.0f : 0.5f);
+  return p1 / (p1 + p2);
+}
+
+// LUT position and crystal of a detected photon on a scanner with gaps.
+// Module m spans azimuth [m mod_phi, (m + 1) mod_phi) as [half gap | module_t
+// crystals | half gap], block b the axial range [b blk_pitch, (b + 1)
+// blk_pitch) in the same way.  Returns crystal | ring << 16 | lost << 31 in
+// the low word (lost: in a gap, gap_mode 1) and tpos | apos << 16 in the high
+// word.  Gap_mode 2 assigns a photon in a transaxial gap with u0, then one in
+// an inner axial gap with the next of (u0, u1); at the scanner's axial ends
+// only one block borders the gap.
+__device__ __noinline__ unsigned long long place(const ScannerParams& S, float phi, float hz, float dx, float dy,
+                                                 float dz, float nx, float ny, float u0, float u1) {
+  const int m = min((int)floorf(phi * S.inv_mod_phi), S.n_mod - 1);
+  const float u = phi - (float)m * S.mod_phi;
+  int tp, bt = 0, cr = 0;
+  float xt = 0.0f;
+  if (u < 0.5f * S.gap_gamma) {
+    tp = 0;
+    bt = m;
+    xt = u * S.radius;
+  } else if (u >= S.mod_phi - 0.5f * S.gap_gamma) {
+    tp = S.module_t + 1;
+    bt = m + 1;
+    xt = (u - S.mod_phi) * S.radius;
+  } else {
+    const int j = max(0, min((int)floorf((u - 0.5f * S.gap_gamma) * S.inv_crys_phi), S.module_t - 1));
+    tp = j + 1;
+    cr = m * S.module_t + j;
+  }
+  const float z = hz + S.half_len;
+  const int b = max(0, min((int)floorf(z * S.inv_blk_pitch), S.n_blk - 1));
+  const float w = z - (float)b * S.blk_pitch;
+  int al, ba = 0, rg = 0;
+  float xa = 0.0f;
+  if (w < 0.5f * S.gap_a) {
+    al = 0;
+    ba = b;
+    xa = w;
+  } else if (w >= S.blk_pitch - 0.5f * S.gap_a) {
+    al = S.module_a + 1;
+    ba = b + 1;
+    xa = w - S.blk_pitch;
+  } else {
+    const int j = max(0, min((int)floorf((w - 0.5f * S.gap_a) * S.inv_ring_w), S.module_a - 1));
+    al = j + 1;
+    rg = b * S.module_a + j;
+  }
+  const unsigned long long pos = (unsigned long long)((uint32_t)tp | (uint32_t)(b * (S.module_a + 2) + al) << 16)
+                                 << 32;
+  const bool gt = tp == 0 || tp == S.module_t + 1, ga = al == 0 || al == S.module_a + 1;
+  if (S.gap_mode == 1) return pos | (gt || ga ? 1ull << 31 : 0ull) | (uint32_t)cr | (uint32_t)rg << 16;
+  const float dn = dx * nx + dy * ny, dt = -dx * ny + dy * nx;
+  if (gt) {
+    const float p1 = edge_prob(S, xt, dt / dn, dn * rsqrtf(dn * dn + dt * dt), S.gap_t_mm);
+    const int c0 = bt * S.module_t;
+    cr = u0 < p1 ? (c0 == 0 ? S.n_crystals - 1 : c0 - 1) : (c0 == S.n_crystals ? 0 : c0);
+  }
+  if (ga) {
+    if (ba == 0) {
+      rg = 0;
+    } else if (ba == S.n_blk) {
+      rg = S.n_rings - 1;
+    } else {
+      const float p1 = edge_prob(S, xa, dz / dn, dn * rsqrtf(dn * dn + dz * dz), S.gap_a);
+      rg = (gt ? u1 : u0) < p1 ? ba * S.module_a - 1 : ba * S.module_a;
+    }
+  }
+  return pos | (uint32_t)cr | (uint32_t)rg << 16;
 }
 
 // incidence angles (degrees) of direction d at the hit with radial unit
@@ -266,7 +364,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         // ---- refill the slot's window: the single Philox evaluation ----
         uint32_t k = U(F_K, g), nb = U(F_NB, g);
         int need = (int)((kNeedNibbles >> (4 * sec)) & 15u);
-        if (sec == kEscape && S.e_res_k > 0.0f) need = 2;  // Box-Muller pair of the energy blur
+        if (sec == kEscape) need = S.escape_words;  // energy blur, edge-crystal draws
         if (sec == kCoinc && !blur) need = 0;
         if (k + need > 4 * nb) {
           const uint32_t hlo = U(F_HLO, g), hhi = U(F_HHI, g), stream = U(F_META, g) >> 4;
@@ -456,6 +554,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           float path = Fv(F_PATH, g);
           const float a = dx * dx + dy * dy;
           int cls = kDetected, cr = 0, rg = 0;
+          uint32_t pos = 0;  // LUT position tpos | apos << 16 (scanners with gaps)
           float nx = 0.0f, ny = 0.0f;
           if (!(a > 0.0f)) {
             cls = kLostAxial;
@@ -481,6 +580,19 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
                 k += 2;
               }
               if (ed < S.e_lo || ed > S.e_hi) cls = kEnergyWindow;
+              if (S.gap_mode && cls == kDetected) {
+                // two words cover both edge draws (the axial one is the second only after a
+                // transaxial one); the window holds them since escape_words counts them
+                const float u0 = S.gap_mode == 2 ? uni(k) : 0.0f, u1 = S.gap_mode == 2 ? uni(k + 1) : 0.0f;
+                const unsigned long long r = place(S, phi, hz, dx, dy, dz, nx, ny, u0, u1);
+                if ((uint32_t)r >> 31) {
+                  cls = kLostAxial;  // lost in a gap
+                } else {
+                  cr = (int)((uint32_t)r & 0xffffu);
+                  rg = (int)(((uint32_t)r >> 16) & 0x7fffu);
+                }
+                pos = (uint32_t)(r >> 32);
+              }
             }
           }
           count(cls == kDetected, kStatDetected);
@@ -490,6 +602,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           } else if (((m >> 3) & 1u) == 0) {  // photon A: keep it, launch photon B back to back
             const uint32_t nint = U(F_CNT, g) >> 16;
             CU(C_ACRG, g) = (uint32_t)cr | (uint32_t)rg << 16 | (nint > 0 ? 1u << 31 : 0u);
+            if (S.gap_mode) CU(C_APOS, g) = pos;
             setC(C_AE, g, e);
             setC(C_APATH, g, path);
             setC(C_ANX, g, nx);
@@ -513,6 +626,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             finish(g, kSameCrystal, -1, 0);
           } else {
             CU(C_BCRG, g) = (uint32_t)cr | (uint32_t)rg << 16;
+            if (S.gap_mode) CU(C_BPOS, g) = pos;
             setC(C_BNX, g, nx);
             setC(C_BNY, g, ny);
             setF(F_PATH, g, path);
@@ -548,8 +662,17 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             float aa, ab, ba, bb;
             angles(Cv(C_ANX, g), Cv(C_ANY, g), make_float3(Cv(C_ADX, g), Cv(C_ADY, g), Cv(C_ADZ, g)), aa, ab);
             angles(Cv(C_BNX, g), Cv(C_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
-            const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_cr % S.module_t, a_rg % S.module_a) *
-                            lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_cr % S.module_t, b_rg % S.module_a);
+            int a_tp = a_cr % S.module_t, a_ap = a_rg % S.module_a, b_tp = b_cr % S.module_t,
+                b_ap = b_rg % S.module_a;
+            if (S.gap_mode) {
+              const uint32_t pa = CU(C_APOS, g), pb = CU(C_BPOS, g);
+              a_tp = (int)(pa & 0xffffu);
+              a_ap = (int)(pa >> 16);
+              b_tp = (int)(pb & 0xffffu);
+              b_ap = (int)(pb >> 16);
+            }
+            const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_tp, a_ap) *
+                            lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_tp, b_ap);
             q = __float2ll_rn(w * 4294967296.0f);
           }
           // lanes that hit the same bin add their weights first, one atomic per bin

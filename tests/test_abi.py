@@ -76,3 +76,32 @@ def test_descriptors_keep_their_host_arrays_alive():
     n = 64 * 64 * 32
     assert int(np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(d.material)).sum()) == expect
     assert m._keep and lu._keep
+
+
+def test_descriptor_layouts_match_header(tmp_path):
+    """Every ctypes descriptor of the binding has the size and field offsets
+    of its C struct, as the host compiler lays it out from include/psc.h."""
+    import ctypes as C
+    import paper_2509_05047_gb300 as psc
+    if shutil.which("gcc") is None:
+        pytest.skip("no host C compiler")
+    pairs = {"ScannerDesc": "psc_scanner_desc", "MaterialsDesc": "psc_materials_desc",
+             "PhantomDesc": "psc_phantom_desc", "LutDesc": "psc_lut_desc", "SimArgs": "psc_sim_args",
+             "Stats": "psc_stats", "FinalizeArgs": "psc_finalize_args", "Request": "psc_request",
+             "ServerConfig": "psc_server_config", "RequestStatus": "psc_request_status"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "psc.h"', "int main(void) {"]
+    expect = []
+    for py, c in pairs.items():
+        cls = getattr(psc, py)
+        lines.append(f'  printf("%zu\\n", sizeof({c}));')
+        expect.append(C.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({c}, {name}));')
+            expect.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == expect

@@ -292,3 +292,62 @@ def test_energy_resolution_variant_matches_oracle():
         assert (g["cls"] == oracle.ENERGY_WINDOW).sum() != (exact["cls"] == oracle.ENERGY_WINDOW).sum()
     finally:
         s.close()
+
+
+def _vacuum_box():
+    return W.phantom_uniform_box(dims=(32, 32, 24), voxel=(4.0, 4.0, 4.0), material=W.MAT_VACUUM, density=0.0)
+
+
+@pytest.mark.parametrize("mode,phantom", [(1, "vacuum"), (2, "vacuum"), (2, "torso")])
+def test_gap_model_matches_oracle(mode, phantom):
+    """Gaps between the 28 modules and 5 blocks of the paper-scale scanner
+    (Sec. 2.2.1-2.2.2).  Mode 1 loses photons in a gap; mode 2 weights them
+    with the LUT value of their virtual crystal and assigns them to an edge
+    crystal from one word of the photon's stream per gap.  Histories match
+    the oracle's one by one, and the sampled histories reach the gaps."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_signa_gaps(gap_mode=mode)
+    mats = W.standard_materials()
+    ph = _vacuum_box() if phantom == "vacuum" else W.phantom_torso()
+    lut = W.lut_signa(sc)
+    s = Session(sc, mats, ph, lut)
+    try:
+        n = 100_000
+        g = s.run(SEED + 31, 0, n)
+        r = oracle.simulate(sc, mats, ph, lut, SEED + 31, 0, n, threads=8, records=True)
+        same = compare_histories(g, r)
+        assert (~same).sum() <= 0.001 * n
+        rec = r["rec"]
+        det = np.flatnonzero((rec["status"] == oracle.DETECTED).any(axis=1))[:4000]
+        in_gap = sum(oracle.place(sc, rec["hit"][i, k])[0] != 0
+                     for i in det for k in range(2) if rec["status"][i, k] == oracle.DETECTED)
+        if mode == 1:
+            assert in_gap == 0 and (g["cls"] == oracle.LOST_AXIAL).sum() > 0.05 * n
+        else:
+            assert in_gap > 100
+            # histories with a photon in a gap are binned and match
+            gap_rows = [i for i in det if (rec["status"][i] == oracle.DETECTED).all()
+                        and any(oracle.place(sc, rec["hit"][i, k])[0] for k in range(2))]
+            gap_rows = np.array(gap_rows)
+            assert same[gap_rows].mean() >= 0.99
+    finally:
+        s.close()
+
+
+def test_gap_scanner_rejects_a_lut_without_virtual_crystals():
+    """The LUT of a scanner with gaps has module_t + 2 transaxial and
+    n_blocks (module_a + 2) axial positions; a gapless LUT is refused."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_signa_gaps(gap_mode=2)
+    plain = W.scanner_signa()
+    s = Session(sc, W.standard_materials(), _vacuum_box(), W.lut_signa(plain))
+    try:
+        with pytest.raises(psc.PscError) as e:
+            s.run(SEED, 0, 1000)
+        assert e.value.code == psc.PSC_EINVAL
+    finally:
+        s.close()
