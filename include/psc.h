@@ -122,10 +122,14 @@ typedef struct {
   const float* activity;       /* host [nz][ny][nx], >= 0, positive sum */
 } psc_phantom_desc;
 
-/* 5D single-photon detection-probability LUT (Sec. 2.2.2). */
+/* 5D single-photon detection-probability LUT (Sec. 2.2.2), multilinear in energy and the
+ * two angles, exact in the crystal position.  The lower-dimensional LUTs of Sec. 2.2.2
+ * (energy only; energy and angles; energy and crystals) are LUTs with one bin on each axis
+ * they drop: constant along an angle axis, position 0 for every photon on a position axis. */
 typedef struct {
   int32_t n_e, n_a, n_b;       /* energy, transaxial angle, axial angle bins */
-  int32_t n_tpos, n_apos;      /* must equal the scanner's module_t, module_a */
+  int32_t n_tpos, n_apos;      /* the scanner's LUT positions: module_t, module_a without gaps,
+                                  module_t + 2, n_blocks (module_a + 2) with gaps; or 1 */
   double e_min, e_max;         /* keV; nodes at bin centres */
   double a_min, a_max;         /* deg */
   double b_min, b_max;         /* deg */

@@ -387,6 +387,8 @@ static void axis_coord(double x, double lo, double hi, int n, int* i0, int* i1, 
 
 double orc_lut_prob(const orc_lut* L, double e, double alpha, double beta, int32_t tpos, int32_t apos) {
   if (L == NULL || L->data == NULL) return 1.0;
+  if (L->n_tpos == 1) tpos = 0;  /* no crystal information on this axis */
+  if (L->n_apos == 1) apos = 0;
   int ie[2], ia[2], ib[2];
   double fe, fa, fb;
   axis_coord(e, L->e_min, L->e_max, L->n_e, &ie[0], &ie[1], &fe);
@@ -706,7 +708,7 @@ int orc_simulate(const orc_scanner* sc, const orc_materials* mat, const orc_phan
   if (lut && lut->data) {
     int nt = sc->gap_mode ? sc->module_t + 2 : sc->module_t;
     int na = sc->gap_mode ? (sc->n_rings / sc->module_a) * (sc->module_a + 2) : sc->module_a;
-    if (lut->n_tpos != nt || lut->n_apos != na) return -1;
+    if ((lut->n_tpos != nt && lut->n_tpos != 1) || (lut->n_apos != na && lut->n_apos != 1)) return -1;
   }
   if (n == 0) return 0;
   sim_ctx X = {sc, mat, ph, alias_prob, alias_idx, lut, NULL, seed, bin_mask};

@@ -92,6 +92,9 @@ typedef struct {
   double a_min, a_max;     /* transaxial incidence angle axis (deg) */
   double b_min, b_max;     /* axial incidence angle axis (deg) */
   const float* data;       /* [n_apos][n_tpos][n_e][n_a][n_b]; NULL => probability 1 */
+  /* Lower-dimensional LUTs (Sec. 2.2.2: energy only; energy and angles; energy and
+   * crystals) have one bin on each axis they drop: constant along an angle axis, and
+   * position 0 for every photon on a position axis (n_tpos or n_apos = 1). */
 } orc_lut;
 
 /* Per-history listmode record (the simulator's listmode of Sec. 2.2.1 plus

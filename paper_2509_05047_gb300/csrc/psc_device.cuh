@@ -174,7 +174,8 @@ __device__ __forceinline__ float lut_prob(const LutParams& L, float e, float a, 
   lut_axis(e, L.e_min, L.e_scale, L.n_e, e0, e1, fe);
   lut_axis(a, L.a_min, L.a_scale, L.n_a, a0, a1, fa);
   lut_axis(b, L.b_min, L.b_scale, L.n_b, b0, b1, fb);
-  const long long base = ((long long)apos * L.n_tpos + tpos) * L.n_e;
+  // a position axis of one bin (a LUT without crystal information) holds position 0
+  const long long base = ((long long)(L.n_apos == 1 ? 0 : apos) * L.n_tpos + (L.n_tpos == 1 ? 0 : tpos)) * L.n_e;
   const long long r00 = ((base + e0) * L.n_a + a0) * L.n_b;
   const long long r01 = ((base + e0) * L.n_a + a1) * L.n_b;
   const long long r10 = ((base + e1) * L.n_a + a0) * L.n_b;

@@ -745,8 +745,8 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
     const psc_scanner_desc& sd = sc->desc;
     const int nt = sd.gap_mode ? sd.module_t + 2 : sd.module_t;
     const int na = sd.gap_mode ? (sd.n_rings / sd.module_a) * (sd.module_a + 2) : sd.module_a;
-    if (lut->desc.n_tpos != nt || lut->desc.n_apos != na)
-      return fail(PSC_EINVAL, "LUT positions (%d, %d) do not match the scanner's (%d, %d)", lut->desc.n_tpos,
+    if ((lut->desc.n_tpos != nt && lut->desc.n_tpos != 1) || (lut->desc.n_apos != na && lut->desc.n_apos != 1))
+      return fail(PSC_EINVAL, "LUT positions (%d, %d) match neither the scanner's (%d, %d) nor 1", lut->desc.n_tpos,
                   lut->desc.n_apos, nt, na);
   }
   if (acc->scanner != a->scanner) return fail(PSC_EINVAL, "accumulator belongs to scanner %d", (int)acc->scanner);

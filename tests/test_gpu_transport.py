@@ -351,3 +351,34 @@ def test_gap_scanner_rejects_a_lut_without_virtual_crystals():
         assert e.value.code == psc.PSC_EINVAL
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("keep,gaps", [(("e",), 0), (("e", "a", "b"), 0), (("e", "t", "z"), 0),
+                                       (("e", "a", "b"), 1), (("e", "t", "z"), 2)])
+def test_lower_dimensional_luts_match_oracle(keep, gaps):
+    """Sec. 2.2.2's lower-dimensional LUTs, made by summing synthetic
+    histograms over the dropped axes: energy only, energy and angles, energy
+    and crystals; the paper pairs the LUTs without crystal information with
+    dropping gap photons and the energy-and-crystal LUT with edge-crystal
+    assignment.  Per-history parity with the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if gaps:
+        sc, ph, n = W.scanner_signa_gaps(gap_mode=gaps), W.phantom_torso(), 100_000
+        full = W.lut_signa(sc)
+    else:
+        sc, ph, n = W.scanner_tiny(), W.phantom_water_cylinder(), 200_000
+        full = W.lut_tiny(sc)
+    inc, det = W.lut_histograms(full, counts=50.0)
+    lut = W.lut_reduced(full, inc, det, keep)
+    mats = W.standard_materials()
+    s = Session(sc, mats, ph, lut)
+    try:
+        g = s.run(SEED + 41, 0, n)
+        r = oracle.simulate(sc, mats, ph, lut, SEED + 41, 0, n, threads=8)
+        same = compare_histories(g, r)
+        assert (~same).sum() <= 0.001 * n
+        assert (r["cls"] == 7).sum() > 0.001 * n
+    finally:
+        s.close()

@@ -200,3 +200,60 @@ def test_lut_degenerate_axes_and_no_lut():
     for a, b in [(-80.0, 10.0), (0.0, 0.0), (85.0, -60.0)]:
         assert oracle.lut_prob(lut, 470.0, a, b, 0, 0) == pytest.approx(0.5 + 0.001 * 45, rel=1e-6)
     assert oracle.lut_prob(None, 470.0, 10.0, 10.0, 0, 0) == 1.0
+
+
+def _lut_copy(lut, data):
+    return W.Lut(lut.n_e, lut.e_min, lut.e_max, data.shape[3], data.shape[4], data.shape[1], data.shape[0],
+                 np.ascontiguousarray(data, dtype=np.float32), lut.a_min, lut.a_max, lut.b_min, lut.b_max)
+
+
+def test_lower_dimensional_lut_equals_full_lut_constant_on_dropped_axes():
+    """Sec. 2.2.2's lower-dimensional LUTs: a LUT with one bin on the
+    position axes gives every history the weight of the full-size LUT whose
+    values repeat that bin at every position (bit for bit: the same entries
+    are read), and one bin on the angle axes that of a full LUT constant in
+    angle (up to the rounding of the multilinear weights)."""
+    sc = W.scanner_tiny()
+    mats, ph = W.standard_materials(), W.phantom_water_cylinder()
+    lut = W.lut_tiny(sc)
+    n = 50_000
+    red_pos = _lut_copy(lut, lut.data[:1, :1])
+    full_pos = _lut_copy(lut, np.broadcast_to(lut.data[:1, :1], lut.data.shape))
+    a = oracle.simulate(sc, mats, ph, red_pos, 9, 0, n, threads=8)
+    b = oracle.simulate(sc, mats, ph, full_pos, 9, 0, n, threads=8)
+    assert (a["key"] >= 0).sum() > 200
+    np.testing.assert_array_equal(a["q"], b["q"])
+    np.testing.assert_array_equal(a["key"], b["key"])
+    red_ang = _lut_copy(lut, lut.data[:, :, :, 3:4, 5:6])
+    full_ang = _lut_copy(lut, np.broadcast_to(lut.data[:, :, :, 3:4, 5:6], lut.data.shape))
+    a = oracle.simulate(sc, mats, ph, red_ang, 9, 0, n, threads=8)
+    b = oracle.simulate(sc, mats, ph, full_ang, 9, 0, n, threads=8)
+    m = a["key"] >= 0
+    np.testing.assert_allclose(a["w"][m], b["w"][m], rtol=1e-12)
+    # and the reduced LUT differs from the full one where the full one varies
+    c = oracle.simulate(sc, mats, ph, lut, 9, 0, n, threads=8)
+    assert not np.allclose(a["w"][m], c["w"][m])
+
+
+def test_reduced_lut_is_the_ratio_of_summed_histograms():
+    """The energy-only and energy+crystal LUTs made from the two histograms
+    equal the ratio of explicit sums over the dropped axes, and the reduced
+    LUT is a detection probability where photons arrived."""
+    sc = W.scanner_tiny()
+    lut = W.lut_tiny(sc)
+    inc, det = W.lut_histograms(lut, counts=5.0)
+    e_only = W.lut_reduced(lut, inc, det, keep=("e",))
+    assert e_only.data.shape == (1, 1, lut.n_e, 1, 1)
+    for ie in (0, 7, lut.n_e - 1):
+        num = sum(int(det[z, t, ie, i, j]) for z in range(lut.n_apos) for t in range(lut.n_tpos)
+                  for i in range(lut.n_a) for j in range(lut.n_b))
+        den = sum(int(inc[z, t, ie, i, j]) for z in range(lut.n_apos) for t in range(lut.n_tpos)
+                  for i in range(lut.n_a) for j in range(lut.n_b))
+        assert e_only.data[0, 0, ie, 0, 0] == np.float32(num / den)
+    e_pos = W.lut_reduced(lut, inc, det, keep=("e", "t", "z"))
+    assert e_pos.data.shape == (lut.n_apos, lut.n_tpos, lut.n_e, 1, 1)
+    z, t, ie = 1, 2, 3
+    num = int(det[z, t, ie].sum())
+    den = int(inc[z, t, ie].sum())
+    assert e_pos.data[z, t, ie, 0, 0] == np.float32(num / den)
+    assert e_pos.data.min() >= 0.0 and e_pos.data.max() <= 1.0

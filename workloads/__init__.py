@@ -412,6 +412,32 @@ def lut_smooth(n_e, n_a, n_b, n_tpos, n_apos, e_min, e_max=511.0, seed=3):
                np.ascontiguousarray(p, dtype=np.float32))
 
 
+def lut_histograms(lut, counts=200.0, seed=11):
+    """Synthetic stand-ins for the two histograms a LUT is made from (Sec.
+    2.2.2): photons reaching the detection cylinder per LUT bin (Poisson,
+    mean `counts` times a seeded factor in [0.5, 1.5)) and those of them
+    detected (binomial at the LUT's probability)."""
+    rng = np.random.default_rng(seed)
+    incident = rng.poisson(counts * rng.uniform(0.5, 1.5, lut.data.shape))
+    detected = rng.binomial(incident, lut.data.astype(np.float64))
+    return incident, detected
+
+
+def lut_reduced(lut, incident, detected, keep):
+    """A lower-dimensional LUT (Sec. 2.2.2): both histograms summed over the
+    axes not in `keep` (of "e", "a", "b", "t", "z": energy, transaxial and
+    axial angle, transaxial and axial position), then divided; 0 where no
+    photon arrived.  A dropped axis keeps one bin."""
+    axes = {"z": 0, "t": 1, "e": 2, "a": 3, "b": 4}
+    drop = tuple(v for k, v in axes.items() if k not in keep)
+    inc = incident.sum(axis=drop, keepdims=True).astype(np.float64)
+    det = detected.sum(axis=drop, keepdims=True).astype(np.float64)
+    p = np.where(inc > 0, det / np.maximum(inc, 1.0), 0.0)
+    n_apos, n_tpos, n_e, n_a, n_b = p.shape
+    return Lut(n_e, lut.e_min, lut.e_max, n_a, n_b, n_tpos, n_apos, np.ascontiguousarray(p, dtype=np.float32),
+               lut.a_min, lut.a_max, lut.b_min, lut.b_max)
+
+
 def lut_tiny(scanner):
     return lut_smooth(16, 8, 8, scanner.n_tpos, scanner.n_apos, scanner.e_lo)
 
