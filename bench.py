@@ -72,23 +72,69 @@ def parse():
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
+    """SM clock and clock-event reasons sampled every 0.2 s while the timed
+    region runs.  NVML is read in-process through ctypes (the call releases
+    the GIL and forks nothing); without NVML, nvidia-smi is run instead."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits, in the order of the columns above
+    BITS = (0x8, 0x40, 0x20, 0x4)
 
     def __init__(self, device_index):
         self.idx = device_index
         self.samples = []
         self.stop = threading.Event()
         self.t = None
+        self.nvml = self._nvml_handle(device_index)
+        self.source = "nvml" if self.nvml else "nvidia-smi"
+
+    @staticmethod
+    def _nvml_handle(idx):
+        import ctypes as C
+        try:
+            lib = C.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = C.c_void_p()
+            try:
+                import torch
+                p = torch.cuda.get_device_properties(idx)
+                bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+                if lib.nvmlDeviceGetHandleByPciBusId_v2(C.c_char_p(bus), C.byref(h)) != 0:
+                    raise OSError
+            except Exception:
+                if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(idx), C.byref(h)) != 0:
+                    return None
+            return lib, h
+        except (OSError, AttributeError):
+            return None
+
+    def _sample_nvml(self):
+        import ctypes as C
+        lib, h = self.nvml
+        sm, mx, why = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if lib.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) != 0:  # 1 = NVML_CLOCK_SM
+            return
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx))
+        try:
+            reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        reasons(h, C.byref(why))
+        self.samples.append([str(sm.value), str(mx.value)] +
+                            ["Active" if why.value & b else "Not Active" for b in self.BITS])
 
     def _run(self):
         while not self.stop.is_set():
             try:
-                out = subprocess.check_output(
-                    ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                     "--format=csv,noheader,nounits"], text=True, timeout=5)
-                self.samples.append([x.strip() for x in out.strip().split(",")])
+                if self.nvml:
+                    self._sample_nvml()
+                else:
+                    out = subprocess.check_output(
+                        ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                         "--format=csv,noheader,nounits"], text=True, timeout=5)
+                    self.samples.append([x.strip() for x in out.strip().split(",")])
             except Exception:
                 pass
             self.stop.wait(0.2)
@@ -112,7 +158,7 @@ class ClockSampler:
                           if len(s) > i + 2 and s[i + 2].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+                "samples": len(self.samples), "source": self.source}
 
 
 def measured_peaks():
@@ -272,36 +318,51 @@ def run_native(a):
 
     # end to end through the host-buffer API: every step a new activity
     # image goes in from the host and the scatter estimate comes back to
-    # pinned host memory.  Steps are pipelined the way a caller would run
-    # them: the read-back of step i (on a copy stream) overlaps step i+1's
-    # transport and smoothing, with two device output buffers taking turns.
+    # page-locked host memory (psc_host_alloc).  Steps are pipelined the way
+    # a caller would run them: the read-back of step i (on a copy stream)
+    # overlaps step i+1's transport and smoothing, with two device output
+    # buffers taking turns.  Like the device-timed steps, W untimed warm-up
+    # steps (with their read-backs) come first: a serving process reuses its
+    # host buffer, and the first copies into a new one can run slower while
+    # the host link's address translations for it are set up.
     e2e = None
     if not a.no_e2e and rank == 0:
-        host_out = torch.empty(sc.shape, dtype=torch.float64, pin_memory=True)
+        host_out = psc.host_tensor(sc.shape, torch.float64)   # page-locked, huge pages
         act = np.ascontiguousarray(ph.activity, dtype=np.float32)
         outs = [out, torch.empty_like(out)]
         copy = torch.cuda.Stream(dev)
-        fin_ev = [torch.cuda.Event() for _ in range(2)]
-        back_ev = [torch.cuda.Event() for _ in range(2)]
-        torch.cuda.synchronize()
-        k = max(2, min(a.steps, 3))
-        t_start = time.perf_counter()
-        for i in range(k):
-            b = i % 2
-            psc.psc_update_activity(ctx, p_id, act)   # waits only for launches reading the phantom
-            if i >= 2:
-                stream.wait_event(back_ev[b])          # the buffer's previous read-back is done
-            step(100 + i, dst=outs[b])
-            fin_ev[b].record(stream)
-            copy.wait_event(fin_ev[b])
-            with torch.cuda.stream(copy):
-                host_out.copy_(outs[b], non_blocking=True)
-            back_ev[b].record(copy)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t_start
+
+        def e2e_run(i0, k):
+            # per step: compute start / end on the step stream, read-back start / end on the copy stream
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k)]
+            torch.cuda.synchronize()
+            t_start = time.perf_counter()
+            for i in range(k):
+                b = i % 2
+                psc.psc_update_activity(ctx, p_id, act)   # waits only for launches reading the phantom
+                if i >= 2:
+                    stream.wait_event(ev[i - 2][3])        # the buffer's previous read-back is done
+                ev[i][0].record(stream)
+                step(i0 + i, dst=outs[b])
+                ev[i][1].record(stream)
+                copy.wait_event(ev[i][1])
+                ev[i][2].record(copy)
+                with torch.cuda.stream(copy):
+                    host_out.copy_(outs[b], non_blocking=True)
+                ev[i][3].record(copy)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t_start, ev
+
+        e2e_run(100, max(1, a.warmup))
+        k = max(2, a.steps)
+        dt, ev = e2e_run(200, k)
+        back_ms = [ev[i][2].elapsed_time(ev[i][3]) for i in range(k)]
         e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": int(act.nbytes),
-               "d2h_bytes_per_step": int(out.numel() * 8), "steps": k,
-               "pipelined": "read-back of step i overlaps step i+1 (two device output buffers)"}
+               "d2h_bytes_per_step": int(out.numel() * 8), "steps": k, "warmup": max(1, a.warmup),
+               "pipelined": "read-back of step i overlaps step i+1 (two device output buffers)",
+               "compute_ms": [round(ev[i][0].elapsed_time(ev[i][1]), 1) for i in range(k)],
+               "readback_ms": [round(x, 1) for x in back_ms],
+               "readback_gbs": round(out.numel() * 8 * k / sum(back_ms) / 1e6, 1)}
         del host_out, outs
 
     peaks, src = measured_peaks()

@@ -164,6 +164,7 @@ typedef struct {
   uint64_t tries;                  /* Compton and Rayleigh rejection-sampling tries */
   uint64_t detected;               /* photons that reached the detector inside the window */
   uint64_t atomics;                /* global atomics issued (events of a warp in one bin share one) */
+  int32_t grid, block;             /* launch shape of the call's (last) transport launch */
 } psc_stats;
 
 /* Sinogram post-processing (Sec. 2.2.4, 2.3.2). */
@@ -339,6 +340,20 @@ int psc_poll(psc_ctx* ctx, uint64_t ticket, psc_request_status* status);
 int psc_wait(psc_ctx* ctx, uint64_t ticket, int64_t timeout_us);
 /* Bytes of device memory held by the context's objects. */
 uint64_t psc_resident_bytes(const psc_ctx* ctx);
+
+/* Page-locked host memory for reading results back (the finalized scatter estimate of
+ * Sec. 2.3 is 8 bytes per sinogram bin, 43.8 GB at the paper's scale).  The buffer is
+ * anonymous memory aligned to and advised for transparent huge pages, faulted in, and
+ * registered with CUDA for every device (cudaHostRegister, portable).  Huge pages keep
+ * the device's translations of the buffer few, so device-to-host copies into it run at
+ * the host link's rate even while kernels run.  Independent of any context.
+ *   bytes: size (> 0; rounded up to whole huge pages).  *ptr: the buffer, owned by the
+ *   caller until psc_host_free.  Errors: PSC_EINVAL (NULL ptr, 0 bytes), PSC_ENOMEM
+ *   (mapping failed), PSC_EDEVICE (registration failed; nothing is left allocated). */
+int psc_host_alloc(uint64_t bytes, void** ptr);
+/* Unregister and unmap a buffer of psc_host_alloc.  PSC_EINVAL for any other pointer
+ * (nothing is freed). */
+int psc_host_free(void* ptr);
 
 #ifdef __cplusplus
 }

@@ -77,12 +77,13 @@ class Stats(C.Structure):
     _fields_ = [("class_counts", C.c_uint64 * 8), ("steps", C.c_uint64), ("compton", C.c_uint64),
                 ("rayleigh", C.c_uint64), ("photo", C.c_uint64), ("binned", C.c_uint64),
                 ("weight_sum", C.c_uint64), ("rng_blocks", C.c_uint64), ("tries", C.c_uint64),
-                ("detected", C.c_uint64), ("atomics", C.c_uint64)]
+                ("detected", C.c_uint64), ("atomics", C.c_uint64), ("grid", C.c_int32),
+                ("block", C.c_int32)]
 
     def as_dict(self):
         d = {k: int(v) for k, v in zip(CLASSES, self.class_counts)}
         for f in ("steps", "compton", "rayleigh", "photo", "binned", "weight_sum", "rng_blocks",
-                  "tries", "detected", "atomics"):
+                  "tries", "detected", "atomics", "grid", "block"):
             d[f] = int(getattr(self, f))
         return d
 
@@ -118,6 +119,8 @@ _P, _I32, _U64 = C.c_void_p, C.c_int32, C.c_uint64
 SIGNATURES = {
     "psc_create": (C.c_int, [C.POINTER(C.c_void_p), _I32, _U64]),
     "psc_destroy": (None, [_P]),
+    "psc_host_alloc": (C.c_int, [_U64, C.POINTER(C.c_void_p)]),
+    "psc_host_free": (C.c_int, [C.c_void_p]),
     "psc_last_error": (C.c_char_p, []),
     "psc_load_scanner": (C.c_int, [_P, C.POINTER(ScannerDesc), C.POINTER(_I32)]),
     "psc_load_materials": (C.c_int, [_P, C.POINTER(MaterialsDesc), C.POINTER(_I32)]),
@@ -206,6 +209,34 @@ def psc_destroy(ctx):
 
 def psc_resident_bytes(ctx):
     return int(lib().psc_resident_bytes(ctx))
+
+
+def psc_host_alloc(nbytes):
+    p = C.c_void_p()
+    _check(lib().psc_host_alloc(int(nbytes), C.byref(p)))
+    return int(p.value)
+
+
+def psc_host_free(ptr):
+    _check(lib().psc_host_free(C.c_void_p(ptr)))
+
+
+def host_tensor(shape, dtype=None):
+    """A CPU tensor over a psc_host_alloc buffer (page-locked, huge pages),
+    freed when the last view of it is collected."""
+    import weakref
+    import numpy as np
+    import torch
+    dtype = dtype or torch.float64
+    n = 1
+    for d in shape:
+        n *= int(d)
+    nbytes = max(1, n * torch.empty((), dtype=dtype).element_size())
+    ptr = psc_host_alloc(nbytes)
+    raw = np.ctypeslib.as_array((C.c_uint8 * nbytes).from_address(ptr))
+    # at interpreter exit CUDA may be gone before the buffer: the return code is dropped
+    weakref.finalize(raw, lambda p=ptr: lib().psc_host_free(C.c_void_p(p)))
+    return torch.from_numpy(raw).view(dtype)[:n].view(tuple(shape))
 
 
 def psc_load_scanner(ctx, desc: ScannerDesc):

@@ -7,6 +7,7 @@
 // on the caller's stream.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -17,6 +18,9 @@
 #include <string>
 #include <unordered_map>
 #include <vector>
+
+#include <sys/mman.h>
+#include <unistd.h>
 
 #include "psc.h"
 #include "psc_internal.h"
@@ -374,6 +378,79 @@ void psc_destroy(psc_ctx* ctx) {
 }
 
 uint64_t psc_resident_bytes(const psc_ctx* ctx) { return ctx ? ctx->resident : 0; }
+
+}  // extern "C"
+
+namespace {
+
+std::mutex g_host_mu;
+std::unordered_map<void*, size_t> g_host;  // buffer -> mapped bytes
+
+// the kernel's transparent huge page size (2 MB where it does not say)
+size_t huge_page_bytes() {
+  size_t hp = 2u << 20;
+  if (FILE* f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+    unsigned long long v = 0;
+    if (std::fscanf(f, "%llu", &v) == 1 && v >= 4096 && (v & (v - 1)) == 0) hp = (size_t)v;
+    std::fclose(f);
+  }
+  return hp;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psc_host_alloc(uint64_t bytes, void** ptr) {
+  if (!ptr) return fail(PSC_EINVAL, "ptr is NULL");
+  *ptr = nullptr;
+  if (bytes == 0) return fail(PSC_EINVAL, "zero bytes");
+  const size_t hp = huge_page_bytes();
+  if (bytes > SIZE_MAX - 2 * hp) return fail(PSC_EOVERFLOW, "%llu bytes", (unsigned long long)bytes);
+  const size_t len = (size_t)((bytes + hp - 1) / hp * hp);
+  // map one huge page more than needed, then trim to a huge-page-aligned range
+  void* raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (raw == MAP_FAILED) return fail(PSC_ENOMEM, "mapping %zu bytes of host memory failed", len + hp);
+  const uintptr_t a = ((uintptr_t)raw + hp - 1) & ~(uintptr_t)(hp - 1);
+  const size_t head = a - (uintptr_t)raw;
+  if (head) munmap(raw, head);
+  if (hp - head) munmap((char*)a + len, hp - head);
+  char* p = (char*)a;
+  madvise(p, len, MADV_HUGEPAGE);  // advice only: without it the buffer still works, on base pages
+  const long pg = sysconf(_SC_PAGESIZE);
+  const size_t step = pg > 0 ? (size_t)pg : 4096;
+  for (size_t i = 0; i < len; i += step) p[i] = 0;  // fault in now, as huge pages where possible
+  const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    munmap(p, len);
+    return cuda_fail(e, "registering host buffer");
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    g_host[p] = len;
+  }
+  *ptr = p;
+  return PSC_OK;
+}
+
+int psc_host_free(void* ptr) {
+  size_t len = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    auto it = g_host.find(ptr);
+    if (it == g_host.end()) return fail(PSC_EINVAL, "%p is not a buffer of psc_host_alloc", ptr);
+    len = it->second;
+    g_host.erase(it);
+  }
+  const cudaError_t e = cudaHostUnregister(ptr);
+  munmap(ptr, len);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "unregistering host buffer");
+  }
+  return PSC_OK;
+}
 
 int psc_load_scanner(psc_ctx* ctx, const psc_scanner_desc* d, int32_t* id) {
   if (!ctx || !id) return fail(PSC_EINVAL, "ctx or id is NULL");
@@ -834,6 +911,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
   }
   // one launch per LUT storage type, at most kMaxJobs jobs each
   std::vector<bool> done(jobs.size(), false);
+  int last_grid = 0;
   for (size_t i0 = 0; i0 < jobs.size(); ++i0) {
     if (done[i0]) continue;
     BatchParams bp;
@@ -891,6 +969,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     bp.cold = (uint32_t*)ctx->cold.p;
     CK(cudaStreamWaitEvent(s, ctx->cold_done, 0), "order slot buffer users");
     CK(launch_transport(bp, dt, grid, block, smem, s), "transport kernel launch");
+    last_grid = grid;
     CK(cudaEventRecord(ctx->cold_done, s), "order slot buffer users");
     for (PhantomObj* ph : used) {  // activity updates wait for this launch
       std::lock_guard<std::mutex> ul(ph->use_mu);
@@ -914,6 +993,8 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     stats->tries = h[kStatTries];
     stats->detected = h[kStatDetected];
     stats->atomics = h[kStatAtomics];
+    stats->grid = last_grid;
+    stats->block = block;
   }
   return PSC_OK;
 }

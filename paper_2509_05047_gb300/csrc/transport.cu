@@ -741,13 +741,24 @@ cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int 
   }
 }
 
-// both instantiations of a LUT type share launch bounds and shared memory
+// both instantiations of a LUT type share launch bounds and shared memory.
+// The query counts dynamic shared memory above 48 KB only once the kernel
+// may use it, so the attribute is set first (else the first launch of a
+// kernel would size its grid for one CTA per SM).
+template <int DT>
+static cudaError_t occupancy_dt(int block, size_t smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<DT, false>, block, smem);
+}
+
 cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* blocks_per_sm) {
   switch (lut_dtype) {
-    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<0, false>, block, smem);
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<1, false>, block, smem);
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<2, false>, block, smem);
-    default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<-1, false>, block, smem);
+    case 0: return occupancy_dt<0>(block, smem, blocks_per_sm);
+    case 1: return occupancy_dt<1>(block, smem, blocks_per_sm);
+    case 2: return occupancy_dt<2>(block, smem, blocks_per_sm);
+    default: return occupancy_dt<-1>(block, smem, blocks_per_sm);
   }
 }
 

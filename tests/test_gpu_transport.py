@@ -85,6 +85,36 @@ def test_result_independent_of_launch_shape_and_partition(tiny):
     assert bool((tiny.acc() == ref).all())
 
 
+_FIRST_LAUNCH = '''
+import json, sys
+sys.path.insert(0, "tests")
+import workloads as W
+from gpu_helpers import Session
+sc = W.scanner_tiny()
+s = Session(sc, W.standard_materials(), W.phantom_water_cylinder(), W.lut_tiny(sc))
+a = s.run(1, 0, 2_000_000, listmode=False)["stats"]
+b = s.run(1, 0, 2_000_000, listmode=False)["stats"]
+print(json.dumps([a["grid"], a["block"], b["grid"], b["block"]]))
+s.close()
+'''
+
+
+def test_first_launch_of_a_process_fills_every_sm_twice():
+    """The automatic launch shape is 512-thread CTAs, two per SM, from the
+    first launch of a fresh process on (the occupancy query counts the
+    kernel's dynamic shared memory only once the kernel may use it)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    import torch
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.check_output([sys.executable, "-c", _FIRST_LAUNCH], cwd=root, text=True, timeout=600)
+    g1, b1, g2, b2 = json.loads(out.strip().splitlines()[-1])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert (g1, b1) == (g2, b2) == (2 * sms, 512)
+
+
 def test_checkpoint_resume_is_bit_identical(tiny):
     import torch
     n = 120_000
