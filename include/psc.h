@@ -137,6 +137,28 @@ typedef struct {
   const float* data;           /* host [n_apos][n_tpos][n_e][n_a][n_b] in [0, 1] */
 } psc_lut_desc;
 
+/* Listmode record of one coincidence (Sec. 2.2.1: the simulator's list of non-random
+ * coincidences), written by the debug path when psc_sim_args.lm_out is set: every
+ * history whose two photons are detected inside the window in different crystals,
+ * whatever its LOR/TOF bin.  Photon A travels along the emission direction, B against it.
+ * 104 bytes, no implicit padding. */
+typedef struct {
+  uint64_t history;            /* history index */
+  int64_t q;                   /* fixed-point weight rint(w 2^32) (0 when out of range) */
+  int32_t voxel;               /* emission voxel, x fastest */
+  int32_t cls;                 /* PSC class: 5 out of range, 6 true, 7 scatter */
+  float delta_mm;              /* (path_A - path_B) / 2, before the TOF blur: the emission-time
+                                  difference of the two detections times c / 2 */
+  float energy_kev[2];         /* exact energies at detection */
+  float phi[2];                /* azimuth of the hit on the detection cylinder, [0, 2 pi) */
+  float z_mm[2];               /* axial coordinate of the hit */
+  float dir[2][3];             /* unit directions at detection */
+  int32_t crystal[2], ring[2]; /* assigned crystal and ring (after gap handling) */
+  uint16_t n_scatter[2];       /* Compton + Rayleigh interactions (saturating at 65535) */
+  uint8_t rayleigh[2];         /* 1 if any of them was a Rayleigh interaction */
+  uint8_t pad[6];
+} psc_listmode_event;
+
 /* One simulation call (Sec. 2.2.1): histories [first_history,
  * first_history + n_histories) of the counter-based random stream keyed by
  * seed.  The result is independent of launch shape and of how the history
@@ -152,6 +174,11 @@ typedef struct {
   int8_t* cls_out;                 /* device [n_histories] history class, or NULL */
   int64_t* key_out;                /* device [n_histories] sinogram bin (-1 unless true/scatter), or NULL */
   int64_t* q_out;                  /* device [n_histories] fixed-point weight rint(w 2^32), or NULL */
+  psc_listmode_event* lm_out;      /* device [lm_capacity] coincidence records, or NULL */
+  uint64_t* lm_count;              /* device counter, required with lm_out: the call adds its number of
+                                      coincidences; record k lands at lm_out[k] while k < lm_capacity
+                                      (in no particular order; sort by history) */
+  uint64_t lm_capacity;
 } psc_sim_args;
 
 typedef struct {

@@ -70,7 +70,27 @@ class SimArgs(C.Structure):
                 ("scanner", C.c_int32), ("phantom", C.c_int32), ("lut", C.c_int32),
                 ("acc", C.c_int32), ("bin_mask", C.c_int32), ("block", C.c_int32),
                 ("grid", C.c_int32), ("cls_out", C.c_void_p), ("key_out", C.c_void_p),
-                ("q_out", C.c_void_p)]
+                ("q_out", C.c_void_p), ("lm_out", C.c_void_p), ("lm_count", C.c_void_p),
+                ("lm_capacity", C.c_uint64)]
+
+
+class ListmodeEvent(C.Structure):
+    """One coincidence of the listmode debug output (psc_listmode_event)."""
+    _fields_ = [("history", C.c_uint64), ("q", C.c_int64), ("voxel", C.c_int32), ("cls", C.c_int32),
+                ("delta_mm", C.c_float), ("energy_kev", C.c_float * 2), ("phi", C.c_float * 2),
+                ("z_mm", C.c_float * 2), ("dir", (C.c_float * 3) * 2), ("crystal", C.c_int32 * 2),
+                ("ring", C.c_int32 * 2), ("n_scatter", C.c_uint16 * 2), ("rayleigh", C.c_uint8 * 2),
+                ("pad", C.c_uint8 * 6)]
+
+
+def listmode_dtype():
+    """numpy dtype with the layout of psc_listmode_event."""
+    import numpy as np
+    return np.dtype([("history", "<u8"), ("q", "<i8"), ("voxel", "<i4"), ("cls", "<i4"),
+                     ("delta_mm", "<f4"), ("energy_kev", "<f4", (2,)), ("phi", "<f4", (2,)),
+                     ("z_mm", "<f4", (2,)), ("dir", "<f4", (2, 3)), ("crystal", "<i4", (2,)),
+                     ("ring", "<i4", (2,)), ("n_scatter", "<u2", (2,)), ("rayleigh", "u1", (2,)),
+                     ("pad", "u1", (6,))])
 
 
 class Stats(C.Structure):
@@ -453,9 +473,12 @@ def lut_desc(lut, dtype=PSC_LUT_F32, ones=False):
 
 
 def sim_args(seed, first, n, scanner, phantom, acc, lut=0, bin_mask=PSC_BIN_SCATTER, block=0,
-             grid=0, cls_out=None, key_out=None, q_out=None):
+             grid=0, cls_out=None, key_out=None, q_out=None, lm_out=None, lm_count=None, lm_capacity=0):
+    """lm_out: a device uint8 tensor of lm_capacity * 104 bytes for listmode
+    records; lm_count: a device int64 tensor of one element (the counter)."""
     return SimArgs(seed, first, n, scanner, phantom, lut, acc, bin_mask, block, grid,
-                   _ptr(cls_out), _ptr(key_out), _ptr(q_out))
+                   _ptr(cls_out), _ptr(key_out), _ptr(q_out), _ptr(lm_out), _ptr(lm_count),
+                   int(lm_capacity))
 
 
 def finalize_args(acc, sens=0, norm=0, sigma=None, scale=1.0, sens_first=False):

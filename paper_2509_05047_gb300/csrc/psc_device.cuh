@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "psc.h"
+
 namespace psc {
 
 constexpr int kMaxMaterials = 8;
@@ -68,6 +70,9 @@ struct LutParams {
   int dtype;                   // -1 none, 0 f32, 1 f16, 2 bf16
   int n_e, n_a, n_b, n_tpos, n_apos;
   float e_min, e_scale, a_min, a_scale, b_min, b_scale;  // g = (x - min) * scale - 0.5
+  // entries between successive transaxial / axial positions; 0 on a position axis of one
+  // bin (a LUT without crystal information), so every photon reads position 0
+  long long t_stride, a_stride;
 };
 
 // one simulation request: histories [first, first + n) of seed's streams
@@ -84,6 +89,14 @@ struct Job {
   int bin_mask;
 };
 
+// optional listmode records of a job (kept out of Job, which the kernel
+// stages in shared memory)
+struct ListmodeOut {
+  psc_listmode_event* out;
+  unsigned long long* count;
+  unsigned long long cap;
+};
+
 constexpr int kMaxJobs = 48;   // jobs per launch (kernel parameter space)
 
 // one persistent launch over the chunks of several jobs; chunk c belongs to
@@ -95,7 +108,9 @@ struct BatchParams {
   unsigned long long* next_chunk;  // work counter, zero at launch
   unsigned long long* stats;       // kStatCount counters or nullptr
   uint32_t* cold;                  // per-CTA slot fields kept out of shared memory
+  ListmodeOut lm[kMaxJobs];
 };
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameter space");
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
@@ -158,11 +173,12 @@ __device__ __forceinline__ void lut_axis(float x, float lo, float scale, int n, 
   f = g - (float)i;
 }
 
+// entry i of the LUT block at p (the element type follows DT)
 template <int DT>
-__device__ __forceinline__ float lut_load(const void* p, long long idx) {
-  if (DT == 0) return __ldg(reinterpret_cast<const float*>(p) + idx);
-  if (DT == 1) return __half2float(__ldg(reinterpret_cast<const __half*>(p) + idx));
-  return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p) + idx));
+__device__ __forceinline__ float lut_load(const void* p, int i) {
+  if (DT == 0) return __ldg(reinterpret_cast<const float*>(p) + i);
+  if (DT == 1) return __half2float(__ldg(reinterpret_cast<const __half*>(p) + i));
+  return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p) + i));
 }
 
 template <int DT>
@@ -174,16 +190,16 @@ __device__ __forceinline__ float lut_prob(const LutParams& L, float e, float a, 
   lut_axis(e, L.e_min, L.e_scale, L.n_e, e0, e1, fe);
   lut_axis(a, L.a_min, L.a_scale, L.n_a, a0, a1, fa);
   lut_axis(b, L.b_min, L.b_scale, L.n_b, b0, b1, fb);
-  // a position axis of one bin (a LUT without crystal information) holds position 0
-  const long long base = ((long long)(L.n_apos == 1 ? 0 : apos) * L.n_tpos + (L.n_tpos == 1 ? 0 : tpos)) * L.n_e;
-  const long long r00 = ((base + e0) * L.n_a + a0) * L.n_b;
-  const long long r01 = ((base + e0) * L.n_a + a1) * L.n_b;
-  const long long r10 = ((base + e1) * L.n_a + a0) * L.n_b;
-  const long long r11 = ((base + e1) * L.n_a + a1) * L.n_b;
-  const float v000 = lut_load<DT>(L.data, r00 + b0), v001 = lut_load<DT>(L.data, r00 + b1);
-  const float v010 = lut_load<DT>(L.data, r01 + b0), v011 = lut_load<DT>(L.data, r01 + b1);
-  const float v100 = lut_load<DT>(L.data, r10 + b0), v101 = lut_load<DT>(L.data, r10 + b1);
-  const float v110 = lut_load<DT>(L.data, r11 + b0), v111 = lut_load<DT>(L.data, r11 + b1);
+  // the (tpos, apos) block, then 32-bit offsets inside it
+  const long long pos = (long long)apos * L.a_stride + (long long)tpos * L.t_stride;
+  const void* p = DT == 0 ? (const void*)(reinterpret_cast<const float*>(L.data) + pos)
+                          : (const void*)(reinterpret_cast<const __half*>(L.data) + pos);
+  const int r00 = (e0 * L.n_a + a0) * L.n_b, r01 = (e0 * L.n_a + a1) * L.n_b;
+  const int r10 = (e1 * L.n_a + a0) * L.n_b, r11 = (e1 * L.n_a + a1) * L.n_b;
+  const float v000 = lut_load<DT>(p, r00 + b0), v001 = lut_load<DT>(p, r00 + b1);
+  const float v010 = lut_load<DT>(p, r01 + b0), v011 = lut_load<DT>(p, r01 + b1);
+  const float v100 = lut_load<DT>(p, r10 + b0), v101 = lut_load<DT>(p, r10 + b1);
+  const float v110 = lut_load<DT>(p, r11 + b0), v111 = lut_load<DT>(p, r11 + b1);
   const float gb = 1.0f - fb, ga = 1.0f - fa, ge = 1.0f - fe;
   const float w00 = gb * v000 + fb * v001, w01 = gb * v010 + fb * v011;
   const float w10 = gb * v100 + fb * v101, w11 = gb * v110 + fb * v111;

@@ -731,6 +731,9 @@ int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* d, int32_t* id) {
   L.a_scale = (float)(d->n_a / (d->a_max - d->a_min));
   L.b_min = (float)d->b_min;
   L.b_scale = (float)(d->n_b / (d->b_max - d->b_min));
+  const long long block = (long long)d->n_e * d->n_a * d->n_b;
+  L.t_stride = d->n_tpos > 1 ? block : 0;
+  L.a_stride = d->n_apos > 1 ? block * d->n_tpos : 0;
   *id = add_object(ctx, o);
   return PSC_OK;
 }
@@ -877,6 +880,7 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   jb.cls_out = a->cls_out;
   jb.key_out = (long long*)a->key_out;
   jb.q_out = (long long*)a->q_out;
+  if (a->lm_out && !a->lm_count) return fail(PSC_EINVAL, "lm_out needs lm_count");
   return PSC_OK;
 }
 
@@ -884,6 +888,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
                        psc_stream stream) {
   if (!ctx || (!args && n > 0) || n < 0) return fail(PSC_EINVAL, "NULL argument or negative count");
   std::vector<Job> jobs;
+  std::vector<ListmodeOut> lms;
   std::vector<int> dts;
   std::vector<std::shared_ptr<PhantomObj>> phs;
   jobs.reserve(n);
@@ -894,6 +899,8 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
     if (rc) return rc;
     if (jb.n == 0) continue;
     jobs.push_back(jb);
+    lms.push_back(ListmodeOut{args[i].lm_out, args[i].lm_out ? (unsigned long long*)args[i].lm_count : nullptr,
+                              args[i].lm_out ? args[i].lm_capacity : 0});
     dts.push_back(dt);
     phs.push_back(get<PhantomObj>(ctx, args[i].phantom, kPhantomObj));
   }
@@ -925,6 +932,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
       done[i] = true;
       used.push_back(phs[i].get());
       bp.jobs[bp.n_jobs] = jobs[i];
+      bp.lm[bp.n_jobs] = lms[i];
       smem = std::max(smem, transport_smem_bytes(jobs[i].ph, block));
       ++bp.n_jobs;
     }

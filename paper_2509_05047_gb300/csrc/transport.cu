@@ -56,11 +56,13 @@ enum : int {
   C_ACRG, C_AE, C_APATH, C_ANX, C_ANY, C_ADX, C_ADY, C_ADZ,  // photon A at the detector
   C_BCRG, C_BNX, C_BNY,                                      // photon B at the detector
   C_APOS, C_BPOS,                                            // LUT positions (scanners with gaps)
+  C_VOX, C_AZ, C_BZ, C_ASC,                                  // listmode records only
   kColdFields
 };
 // F_META = state | photon << 3 | stream << 4;  F_CNT = steps | interactions << 16;
 // C_ACRG = crystal | ring << 16 | scattered << 31;  C_BCRG = crystal | ring << 16;
-// C_APOS, C_BPOS = tpos | apos << 16;
+// C_APOS, C_BPOS = tpos | apos << 16;  C_ASC = photon A's F_CNT >> 15;
+// listmode runs flag a Rayleigh interaction in bit 15 of F_CNT (steps stay below 2^15)
 // F_TRIES = tries (| material << 16 for a pending Rayleigh event)
 __host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
   return (uint32_t)state | (uint32_t)photon << 3 | (uint32_t)stream << 4;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     __syncthreads();
     const int jcur = s_j;
     if (jcur < 0) break;
+    const ListmodeOut lm = kDebug ? B.lm[jcur] : ListmodeOut{nullptr, nullptr, 0};
     if (jcur != cached) {  // stage the job and its phantom's tables
       const int* src = reinterpret_cast<const int*>(&B.jobs[jcur]);
       for (int i = tid; i < (int)(sizeof(Job) / sizeof(int)); i += bdim)
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           setC(C_D0X, g, dx);
           setC(C_D0Y, g, dy);
           setC(C_D0Z, g, dz);
+          if (kDebug && lm.out) CU(C_VOX, g) = (uint32_t)v;
           setF(F_PX, g, ex);
           setF(F_PY, g, ey);
           setF(F_PZ, g, ez);
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         if (sec == kStep) {
           bool moved = false, ended = false;
           const uint32_t cnt = U(F_CNT, g);
-          if ((int)(cnt & 0xffffu) >= kMaxSteps) {
+          if ((int)(cnt & 0x7fffu) >= kMaxSteps) {
             finish(g, kStepLimit, -1, 0);
           } else {
             const float e = Fv(F_E, g);
@@ -538,7 +542,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             setF(F_DX, g, d.x);
             setF(F_DY, g, d.y);
             setF(F_DZ, g, d.z);
-            U(F_CNT, g) += 1u << 16;
+            U(F_CNT, g) = (U(F_CNT, g) + (1u << 16)) | (kDebug ? 0x8000u : 0u);
             U(F_META, g) = (U(F_META, g) & ~7u) | kStep;
           } else {
             U(F_TRIES, g) = tries;
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           const float a = dx * dx + dy * dy;
           int cls = kDetected, cr = 0, rg = 0;
           uint32_t pos = 0;  // LUT position tpos | apos << 16 (scanners with gaps)
-          float nx = 0.0f, ny = 0.0f;
+          float nx = 0.0f, ny = 0.0f, hz_det = 0.0f;
           if (!(a > 0.0f)) {
             cls = kLostAxial;
           } else {
@@ -564,6 +568,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             const float sq = sqrtf(fmaxf(b * b - a * c, 0.0f));
             const float t = (b >= 0.0f) ? (-c) / (b + sq) : (sq - b) / a;
             const float hx = px + t * dx, hy = py + t * dy, hz = pz + t * dz;
+            hz_det = hz;
             path += t;
             if (!(hz >= -S.half_len && hz < S.half_len)) {
               cls = kLostAxial;
@@ -603,6 +608,10 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             const uint32_t nint = U(F_CNT, g) >> 16;
             CU(C_ACRG, g) = (uint32_t)cr | (uint32_t)rg << 16 | (nint > 0 ? 1u << 31 : 0u);
             if (S.gap_mode) CU(C_APOS, g) = pos;
+            if (kDebug && lm.out) {
+              setC(C_AZ, g, hz_det);
+              CU(C_ASC, g) = U(F_CNT, g) >> 15;
+            }
             setC(C_AE, g, e);
             setC(C_APATH, g, path);
             setC(C_ANX, g, nx);
@@ -627,6 +636,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           } else {
             CU(C_BCRG, g) = (uint32_t)cr | (uint32_t)rg << 16;
             if (S.gap_mode) CU(C_BPOS, g) = pos;
+            if (kDebug && lm.out) setC(C_BZ, g, hz_det);
             setC(C_BNX, g, nx);
             setC(C_BNY, g, ny);
             setF(F_PATH, g, path);
@@ -658,7 +668,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           const int cls = key_ < 0 ? kOutOfRange : scattered ? kScatter : kTrue;
           const bool take = cls == kScatter ? (J.bin_mask & 1) : cls == kTrue ? (J.bin_mask & 2) : false;
           long long q = 0;
-          if (key_ >= 0 && (take || (kDebug && J.q_out))) {
+          if (key_ >= 0 && (take || (kDebug && (J.q_out || lm.out)))) {
             float aa, ab, ba, bb;
             angles(Cv(C_ANX, g), Cv(C_ANY, g), make_float3(Cv(C_ADX, g), Cv(C_ADY, g), Cv(C_ADZ, g)), aa, ab);
             angles(Cv(C_BNX, g), Cv(C_BNY, g), make_float3(Fv(F_DX, g), Fv(F_DY, g), Fv(F_DZ, g)), ba, bb);
@@ -674,6 +684,40 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_tp, a_ap) *
                             lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_tp, b_ap);
             q = __float2ll_rn(w * 4294967296.0f);
+          }
+          if (kDebug && lm.out) {
+            const unsigned long long slot = atomicAdd(lm.count, 1ull);
+            if (slot < lm.cap) {
+              psc_listmode_event* r = lm.out + slot;
+              r->history = (unsigned long long)U(F_HHI, g) << 32 | U(F_HLO, g);
+              r->q = key_ < 0 ? 0 : q;
+              r->voxel = (int)CU(C_VOX, g);
+              r->cls = cls;
+              r->delta_mm = 0.5f * (a_path - path);
+              r->energy_kev[0] = Cv(C_AE, g);
+              r->energy_kev[1] = Fv(F_E, g);
+              float pa = atan2f(Cv(C_ANY, g), Cv(C_ANX, g)), pb = atan2f(Cv(C_BNY, g), Cv(C_BNX, g));
+              r->phi[0] = pa < 0.0f ? pa + 6.283185307179586f : pa;
+              r->phi[1] = pb < 0.0f ? pb + 6.283185307179586f : pb;
+              r->z_mm[0] = Cv(C_AZ, g);
+              r->z_mm[1] = Cv(C_BZ, g);
+              r->dir[0][0] = Cv(C_ADX, g);
+              r->dir[0][1] = Cv(C_ADY, g);
+              r->dir[0][2] = Cv(C_ADZ, g);
+              r->dir[1][0] = Fv(F_DX, g);
+              r->dir[1][1] = Fv(F_DY, g);
+              r->dir[1][2] = Fv(F_DZ, g);
+              r->crystal[0] = a_cr;
+              r->crystal[1] = b_cr;
+              r->ring[0] = a_rg;
+              r->ring[1] = b_rg;
+              const uint32_t sa = CU(C_ASC, g), sb = U(F_CNT, g) >> 15;
+              r->n_scatter[0] = (uint16_t)min(sa >> 1, 65535u);
+              r->n_scatter[1] = (uint16_t)min(sb >> 1, 65535u);
+              r->rayleigh[0] = (uint8_t)(sa & 1u);
+              r->rayleigh[1] = (uint8_t)(sb & 1u);
+              for (int b = 0; b < 6; ++b) r->pad[b] = 0;
+            }
           }
           // lanes that hit the same bin add their weights first, one atomic per bin
           const unsigned act = __activemask();
@@ -727,7 +771,8 @@ static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t s
 template <int DT>
 static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t smem, cudaStream_t s) {
   bool debug = p.stats != nullptr;
-  for (int j = 0; j < p.n_jobs; ++j) debug |= p.jobs[j].cls_out || p.jobs[j].key_out || p.jobs[j].q_out;
+  for (int j = 0; j < p.n_jobs; ++j)
+    debug |= p.jobs[j].cls_out || p.jobs[j].key_out || p.jobs[j].q_out || p.lm[j].out;
   return debug ? launch_dt<DT, true>(p, grid, block, smem, s) : launch_dt<DT, false>(p, grid, block, smem, s);
 }
 

@@ -88,7 +88,8 @@ def test_descriptor_layouts_match_header(tmp_path):
     pairs = {"ScannerDesc": "psc_scanner_desc", "MaterialsDesc": "psc_materials_desc",
              "PhantomDesc": "psc_phantom_desc", "LutDesc": "psc_lut_desc", "SimArgs": "psc_sim_args",
              "Stats": "psc_stats", "FinalizeArgs": "psc_finalize_args", "Request": "psc_request",
-             "ServerConfig": "psc_server_config", "RequestStatus": "psc_request_status"}
+             "ServerConfig": "psc_server_config", "RequestStatus": "psc_request_status",
+             "ListmodeEvent": "psc_listmode_event"}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "psc.h"', "int main(void) {"]
     expect = []
     for py, c in pairs.items():
@@ -105,3 +106,8 @@ def test_descriptor_layouts_match_header(tmp_path):
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert got == expect
+    # the numpy record type of the listmode output has the same layout
+    dt = psc.listmode_dtype()
+    ev = psc.ListmodeEvent
+    assert dt.itemsize == C.sizeof(ev) == 104
+    assert [dt.fields[n][1] for n, _ in ev._fields_] == [getattr(ev, n).offset for n, _ in ev._fields_]

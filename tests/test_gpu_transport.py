@@ -412,3 +412,78 @@ def test_lower_dimensional_luts_match_oracle(keep, gaps):
         assert (r["cls"] == 7).sum() > 0.001 * n
     finally:
         s.close()
+
+
+def test_listmode_records_match_oracle(tiny):
+    """The listmode debug output (Sec. 2.2.1: the simulator's list of
+    coincidences): one record per history whose photons are both detected
+    in different crystals, holding the emission voxel, the exact energies,
+    the cylindrical hit coordinates, the directions, the scatter counts and
+    Rayleigh flags, and the crystals of the oracle's record of the same
+    history; the records' weights and classes are those of the per-history
+    outputs."""
+    import torch
+    n, cap = 150_000, 150_000
+    dev = torch.device("cuda:0")
+    dt = psc.listmode_dtype()
+    lm = torch.zeros(cap * dt.itemsize, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    cls = torch.full((n,), -1, dtype=torch.int8, device=dev)
+    q = torch.full((n,), -2, dtype=torch.int64, device=dev)
+    key = torch.full((n,), -2, dtype=torch.int64, device=dev)
+    tiny.zero()
+    args = psc.sim_args(SEED + 51, 0, n, tiny.s_id, tiny.p_id, tiny.a_id, lut=tiny.l_id,
+                        bin_mask=psc.PSC_BIN_SCATTER | psc.PSC_BIN_TRUES, cls_out=cls, key_out=key,
+                        q_out=q, lm_out=lm, lm_count=cnt, lm_capacity=cap)
+    psc.psc_simulate(tiny.ctx, args, stream=tiny.stream())
+    torch.cuda.synchronize()
+    g_cls, g_q, m = cls.cpu().numpy(), q.cpu().numpy(), int(cnt.item())
+    rec = np.frombuffer(lm[: m * dt.itemsize].cpu().numpy().tobytes(), dtype=dt)
+    rec = rec[np.argsort(rec["history"])]
+    coinc = np.flatnonzero(np.isin(g_cls, [5, 6, 7]))
+    assert m == coinc.size > 1000
+    np.testing.assert_array_equal(rec["history"], coinc)
+    np.testing.assert_array_equal(rec["cls"], g_cls[coinc])
+    in_range = rec["cls"] != 5
+    np.testing.assert_array_equal(rec["q"][in_range], g_q[coinc][in_range])
+    assert (rec["pad"] == 0).all()
+    r = oracle.simulate(tiny.sc, tiny.mats, tiny.ph, tiny.lut, SEED + 51, 0, n, threads=8, records=True)["rec"]
+    o = r[coinc]
+    same = (o["cls"] == rec["cls"]) & (o["key"] == key.cpu().numpy()[coinc])
+    assert same.mean() > 0.999
+    o, g = o[same], rec[same]
+    np.testing.assert_array_equal(g["voxel"], o["voxel"])
+    np.testing.assert_array_equal(g["crystal"], o["crystal"])
+    np.testing.assert_array_equal(g["ring"], o["ring"])
+    np.testing.assert_array_equal(g["n_scatter"], o["n_compton"] + o["n_rayleigh"])
+    np.testing.assert_array_equal(g["rayleigh"], (o["n_rayleigh"] > 0).astype(np.uint8))
+    np.testing.assert_allclose(g["energy_kev"], o["energy"], rtol=2e-5)
+    np.testing.assert_allclose(g["dir"], o["exit_dir"], atol=2e-5)
+    phi = np.mod(np.arctan2(o["hit"][..., 1], o["hit"][..., 0]), 2 * np.pi)
+    dphi = np.abs(g["phi"] - phi)
+    assert np.minimum(dphi, 2 * np.pi - dphi).max() < 1e-4
+    np.testing.assert_allclose(g["z_mm"], o["hit"][..., 2], atol=2e-3)
+    np.testing.assert_allclose(g["delta_mm"], 0.5 * (o["path"][:, 0] - o["path"][:, 1]), atol=5e-3)
+    assert (g["n_scatter"] > 0).any() and (g["n_scatter"] == 0).any()
+
+
+def test_listmode_capacity_counts_beyond_the_buffer(tiny):
+    """Records past lm_capacity are counted but not written; lm_out needs
+    lm_count."""
+    import torch
+    dev = torch.device("cuda:0")
+    dt = psc.listmode_dtype()
+    cap = 10
+    lm = torch.full(((cap + 1) * dt.itemsize,), 0xAB, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    args = psc.sim_args(SEED + 52, 0, 50_000, tiny.s_id, tiny.p_id, tiny.a_id, lut=tiny.l_id,
+                        lm_out=lm, lm_count=cnt, lm_capacity=cap)
+    psc.psc_simulate(tiny.ctx, args, stream=tiny.stream())
+    torch.cuda.synchronize()
+    assert int(cnt.item()) > cap
+    tail = lm[cap * dt.itemsize:].cpu().numpy()
+    assert (tail == 0xAB).all()  # the record after the capacity is untouched
+    bad = psc.sim_args(SEED, 0, 10, tiny.s_id, tiny.p_id, tiny.a_id, lm_out=lm, lm_capacity=cap)
+    with pytest.raises(psc.PscError) as e:
+        psc.psc_simulate(tiny.ctx, bad, stream=tiny.stream())
+    assert e.value.code == psc.PSC_EINVAL
