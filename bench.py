@@ -199,6 +199,50 @@ def transport_ops(st):
             + OPS_PER_DETECTION * det + OPS_PER_HISTORY * hist)
 
 
+def transport_bounds(psc, st, kern_ms, big, stream):
+    """The transport's random-access rates against what the device sustains:
+    int64 atomic adds spread over a sinogram-sized buffer (the output buffer,
+    viewed as int64, stands in for the accumulator) and 4-byte gathers from a
+    64 MB table (the size of the phantom, alias table and LUT together).  The
+    transport's rates come from its device counters over the mean timed
+    launch: one atomic per bin a warp adds to, an alias entry per history, a
+    material and a density per Woodcock step, and 8 LUT taps per photon of a
+    binned coincidence."""
+    import torch
+    sh = stream.cuda_stream
+    buf = big.view(torch.int64).view(-1)
+    table = torch.rand(16 << 20, device=big.device)
+    sink = torch.zeros(1, device=big.device)
+    grid, block = 152 * 8, 256
+
+    def timed(fn, per_thread, reps=3):
+        fn(per_thread)                                   # warm-up
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(per_thread)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return grid * block * per_thread / best
+
+    atom_peak = timed(lambda k: psc.psc_peak_random_atomics(buf, grid, block, k, seed=7, stream=sh), 256)
+    gath_peak = timed(lambda k: psc.psc_peak_random_gather(table, sink, grid, block, k, seed=7, stream=sh), 512)
+    del table
+    hist = sum(st[c] for c in ("absorbed", "lost_axial", "energy_window", "step_limit",
+                                "same_crystal", "out_of_range", "true", "scatter"))
+    kern_s = kern_ms / 1e3
+    atom = st["atomics"] / kern_s
+    gath = (hist + 2 * st["steps"] + 16 * st["binned"]) / kern_s
+    return {"atomics": {"achieved": round(atom / 1e9, 4), "peak": round(atom_peak / 1e9, 3), "unit": "G/s",
+                        "frac": round(atom / atom_peak, 4),
+                        "peak_source": "random int64 atomicAdd over a 43.8 GB buffer (psc_peak_random_atomics)"},
+            "l2_gathers": {"achieved": round(gath / 1e9, 3), "peak": round(gath_peak / 1e9, 2), "unit": "G/s",
+                           "frac": round(gath / gath_peak, 4),
+                           "peak_source": "random 4-byte loads from a 64 MB table (psc_peak_random_gather)"}}
+
+
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
@@ -315,6 +359,7 @@ def run_native(a):
         ms = float(t.item())
     ms_step = ms / a.steps
     value = world * n * a.steps / (ms / 1e3)
+    bounds = transport_bounds(psc, st, kern_ms, out, stream) if rank == 0 else None
 
     # end to end through the host-buffer API: every step a new activity
     # image goes in from the host and the scatter estimate comes back to
@@ -389,7 +434,8 @@ def run_native(a):
                       "l2": f"inputs larger than L2 ({sc.n_bins * 8 / 1e9:.1f} GB accumulator + "
                             f"{sc.n_bins * 8 / 1e9:.1f} GB output streamed every step)",
                       "parallelism": f"replicas{world}"},
-           "roofline": roofline, "finalize_roofline": finalize_roofline, "clocks": clocks, "e2e": e2e,
+           "roofline": roofline, "finalize_roofline": finalize_roofline, "transport_bounds": bounds,
+           "clocks": clocks, "e2e": e2e,
            "gpu_launches": 4 * a.steps,
            "phases_ms": {"acc_zero": round(float(phase[0]), 3), "transport": round(float(phase[1]), 3),
                          "finalize": round(float(phase[2]), 3)},

@@ -139,6 +139,9 @@ _P, _I32, _U64 = C.c_void_p, C.c_int32, C.c_uint64
 SIGNATURES = {
     "psc_create": (C.c_int, [C.POINTER(C.c_void_p), _I32, _U64]),
     "psc_destroy": (None, [_P]),
+    "psc_peak_random_atomics": (C.c_int, [C.c_void_p, _U64, _I32, _I32, _I32, _U64, C.c_void_p]),
+    "psc_peak_random_gather": (C.c_int, [C.c_void_p, C.c_uint32, _I32, _I32, _I32, _U64, C.c_void_p,
+                                         C.c_void_p]),
     "psc_host_alloc": (C.c_int, [_U64, C.POINTER(C.c_void_p)]),
     "psc_host_free": (C.c_int, [C.c_void_p]),
     "psc_last_error": (C.c_char_p, []),
@@ -229,6 +232,18 @@ def psc_destroy(ctx):
 
 def psc_resident_bytes(ctx):
     return int(lib().psc_resident_bytes(ctx))
+
+
+def psc_peak_random_atomics(buf, grid, block, per_thread, seed=1, stream=None):
+    """Measurement kernel: random int64 atomic adds into the device tensor buf."""
+    _check(lib().psc_peak_random_atomics(_ptr(buf), buf.numel(), grid, block, per_thread, seed,
+                                         _stream(stream)))
+
+
+def psc_peak_random_gather(table, sink, grid, block, per_thread, seed=1, stream=None):
+    """Measurement kernel: random 4-byte gathers from the device float tensor table."""
+    _check(lib().psc_peak_random_gather(_ptr(table), table.numel(), grid, block, per_thread, seed,
+                                        _ptr(sink), _stream(stream)))
 
 
 def psc_host_alloc(nbytes):

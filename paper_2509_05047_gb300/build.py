@@ -28,8 +28,8 @@ def sources():
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(HERE, "csrc", "*.h*")) + [
-        os.path.join(ROOT, "include", "psc.h"), os.path.abspath(__file__)]
+    return sources() + glob.glob(os.path.join(HERE, "csrc", "*.h*")) + \
+        glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
 def nvcc():

@@ -13,6 +13,9 @@ struct psc_ctx;
 
 namespace psc {
 
+// set the calling thread's psc_last_error message; returns code
+int set_error(int code, const char* msg);
+
 struct FinParams {
   const long long* acc;
   double* out;

@@ -45,6 +45,14 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(PSC_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+namespace psc {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace psc
+
+namespace {
+
 #define CK(call, what)                                   \
   do {                                                   \
     cudaError_t e_ = (call);                             \

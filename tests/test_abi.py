@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads without a
 GPU, and exports every entry point that include/psc.h declares; the Python
 binding names the same entry points."""
+import glob
 import os
 import re
 import shutil
@@ -12,9 +13,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "psc.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(psc_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(psc_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
