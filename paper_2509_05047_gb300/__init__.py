@@ -139,6 +139,8 @@ _P, _I32, _U64 = C.c_void_p, C.c_int32, C.c_uint64
 SIGNATURES = {
     "psc_create": (C.c_int, [C.POINTER(C.c_void_p), _I32, _U64]),
     "psc_destroy": (None, [_P]),
+    "psc_check_philox": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "psc_check_curand_philox": (C.c_int, [_U64, _U64, _I32, C.c_void_p]),
     "psc_peak_random_atomics": (C.c_int, [C.c_void_p, _U64, _I32, _I32, _I32, _U64, C.c_void_p]),
     "psc_peak_random_gather": (C.c_int, [C.c_void_p, C.c_uint32, _I32, _I32, _I32, _U64, C.c_void_p,
                                          C.c_void_p]),
@@ -232,6 +234,21 @@ def psc_destroy(ctx):
 
 def psc_resident_bytes(ctx):
     return int(lib().psc_resident_bytes(ctx))
+
+
+def psc_check_philox(ctr_key):
+    """The transport kernel's Philox4x32-10 on rows (c0, c1, c2, c3, k0, k1)."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((a.shape[0], 4), dtype=np.uint32)
+    _check(lib().psc_check_philox(a.ctypes.data, a.shape[0], out.ctypes.data))
+    return out
+
+
+def psc_check_curand_philox(seed, subsequence, n_blocks):
+    """cuRAND's Philox4_32_10: n_blocks curand4 draws after curand_init(seed, subsequence, 0)."""
+    out = np.zeros((n_blocks, 4), dtype=np.uint32)
+    _check(lib().psc_check_curand_philox(seed, subsequence, n_blocks, out.ctypes.data))
+    return out
 
 
 def psc_peak_random_atomics(buf, grid, block, per_thread, seed=1, stream=None):
