@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--gaps", type=int, default=0, choices=[0, 1, 2],
                     help="gaps between modules and blocks: 1 loses photons in a gap, 2 assigns them "
                          "to edge crystals (paper-scale workload; 2 mm gaps, 18 x 55 LUT positions)")
+    ap.add_argument("--reference-histories", type=float, default=1e10,
+                    help="precision study: histories of the FP32 reference estimate")
     ap.add_argument("--precision-workload", default="small", choices=["small", "paper"],
                     help="precision study on the small configuration (water cylinder, 288 x 16 "
                          "scanner) or the paper-scale one")
@@ -549,7 +551,7 @@ def run_precision(a):
             den += float((rf[i:i + (1 << 28)] ** 2).sum())
         return math.sqrt(num / den) if den > 0 else float("nan")
 
-    n_ref = int(a.histories)
+    n_ref = int(a.reference_histories)
     ref = torch.empty(sc.shape, dtype=torch.float64, device=dev)
     t = time.perf_counter()
     estimate(n_ref, luts["f32"], 777, ref)

@@ -89,6 +89,63 @@ __global__ void rotate_sum_kernel(const long long* __restrict__ in, long long* _
   out[(((long long)p * V + v) * R + r) * T + t] = sum;
 }
 
+// bin index of the LOR (a + c, b + c) mod n of plane (ra, rb) and TOF bin t:
+// when the order reverses, the rings swap and the TOF bin mirrors
+__device__ __forceinline__ long long rotated_bin(int n, int n_rings, int R, int T, int rad_off, int a2, int b2,
+                                                 int ra, int rb, int t) {
+  const bool flip = a2 > b2;
+  const int lo = flip ? b2 : a2, hi = flip ? a2 : b2;
+  int f = lo + hi, s = 1;
+  if (f >= n) {
+    f -= n;
+    s = -1;
+  }
+  const int v2 = f >> 1;
+  const int r2 = s * (n / 2 - (hi - lo)) + n / 2 - 1 - rad_off;
+  const long long p2 = flip ? (long long)rb * n_rings + ra : (long long)ra * n_rings + rb;
+  const int t2 = flip ? T - 1 - t : t;
+  return ((p2 * (n / 2) + v2) * R + r2) * T + t2;
+}
+
+// The same sum, one orbit at a time, for n / step even.  A rotation by
+// step crystals moves an LOR by step views, so every orbit has members in
+// views [0, step): an LOR x and its half-turn partner (rotation by n / 2
+// crystals).  The one of the two with the lower bin index sums the input
+// over the n / step rotations of x and writes that sum to every member of
+// the orbit (the sum is the same for all of them): one read and one write
+// per bin.  grid (ceil(R T / 256), step, planes)
+__global__ void rotate_orbit_kernel(const long long* __restrict__ in, long long* __restrict__ out, int n,
+                                    int n_rings, int R, int T, int step) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R * T) return;
+  const int r = c / T, t = c - r * T;
+  const int v = blockIdx.y;
+  const int p = blockIdx.z;
+  const int ra = p / n_rings, rb = p - ra * n_rings;
+  const int rad_off = (n - 1 - R) / 2;
+  int a, b;
+  lor_crystals(n, v, r + rad_off, a, b);
+  const int h = n / 2;
+  const long long self = (((long long)p * h + v) * R + r) * T + t;
+  const long long partner =
+      rotated_bin(n, n_rings, R, T, rad_off, a + h >= n ? a + h - n : a + h, b + h >= n ? b + h - n : b + h, ra, rb, t);
+  if (partner < self) return;
+  long long sum = 0;
+  int a2 = a, b2 = b;
+  for (int k = 0; k < n / step; ++k, a2 += step, b2 += step) {
+    if (a2 >= n) a2 -= n;
+    if (b2 >= n) b2 -= n;
+    sum += __ldg(in + rotated_bin(n, n_rings, R, T, rad_off, a2, b2, ra, rb, t));
+  }
+  a2 = a;
+  b2 = b;
+  for (int k = 0; k < n / step; ++k, a2 += step, b2 += step) {
+    if (a2 >= n) a2 -= n;
+    if (b2 >= n) b2 -= n;
+    out[rotated_bin(n, n_rings, R, T, rad_off, a2, b2, ra, rb, t)] = sum;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
@@ -100,8 +157,12 @@ cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, 
 
 cudaError_t launch_rotate_sum(const long long* in, long long* out, int n_crystals, int n_rings, int R, int T,
                               int step, cudaStream_t s) {
-  rotate_sum_kernel<<<dim3((R * T + 255) / 256, n_crystals / 2, n_rings * n_rings), 256, 0, s>>>(
-      in, out, n_crystals, n_rings, R, T, step);
+  if ((n_crystals / step) % 2 == 0)
+    rotate_orbit_kernel<<<dim3((R * T + 255) / 256, step, n_rings * n_rings), 256, 0, s>>>(in, out, n_crystals,
+                                                                                          n_rings, R, T, step);
+  else
+    rotate_sum_kernel<<<dim3((R * T + 255) / 256, n_crystals / 2, n_rings * n_rings), 256, 0, s>>>(
+        in, out, n_crystals, n_rings, R, T, step);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,9 @@ def test_mashing_matches_oracle(env, vf, tf):
     assert e.value.code == psc.PSC_EINVAL
 
 
-@pytest.mark.parametrize("n_crystals,n_rad,step", [(36, 29, 6), (36, 35, 4), (38, 33, 19)])
+# n / step even: one thread per orbit; odd: one thread per output bin
+@pytest.mark.parametrize("n_crystals,n_rad,step", [(36, 29, 6), (36, 35, 4), (38, 33, 19), (36, 29, 2),
+                                                   (36, 33, 18), (40, 39, 8), (40, 37, 5)])
 def test_rotation_sum_matches_oracle(env, n_crystals, n_rad, step):
     ctx, torch = env
     sc = W.scanner_small(n_crystals=n_crystals, n_rings=3, n_tof=4, n_rad=n_rad)
