@@ -24,10 +24,18 @@ __global__ void mash_kernel(const long long* __restrict__ in, long long* __restr
   const int r = c / T2, t2 = c - r * T2;
   const long long p = blockIdx.z;
   const int v2 = blockIdx.y;
+  const long long* row0 = in + ((p * V + (long long)v2 * vf) * R + r) * T + (long long)t2 * tf;
+  const long long vstride = (long long)R * T;
   long long sum = 0;
-  for (int j = 0; j < vf; ++j) {
-    const long long* row = in + ((p * V + (long long)v2 * vf + j) * R + r) * T + (long long)t2 * tf;
-    for (int u = 0; u < tf; ++u) sum += __ldg(row + u);
+  if (tf == 1 && vf <= 8) {  // all loads of the block in flight at once
+    long long x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = j < vf ? __ldg(row0 + j * vstride) : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sum += x[j];
+  } else {
+    for (int j = 0; j < vf; ++j)
+      for (int u = 0; u < tf; ++u) sum += __ldg(row0 + j * vstride + u);
   }
   out[((p * V2 + v2) * R + r) * T2 + t2] = sum;
 }
