@@ -328,29 +328,26 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
 
     for (;;) {
       const int st0 = (int)(U(F_META, g0) & 7u), st1 = (int)(U(F_META, g1) & 7u);
-      if (!__any_sync(0xffffffffu, st0 != kDone || st1 != kDone)) break;
 
       // ---- warp vote: the section that the most slots wait for ----
-      int sec = -1, best = 0;
-      unsigned sm0 = 0, sm1 = 0;
+      // slot counts per section, one byte each (at most 64 slots): sections
+      // 0..3 in lo, 4..5 in hi, summed over the warp by two reductions
+      const unsigned lo = (st0 < 4 ? 1u << (8 * st0) : 0u) + (st1 < 4 ? 1u << (8 * st1) : 0u);
+      const unsigned hi = (st0 >= 4 && st0 < kNumSections ? 1u << (8 * (st0 - 4)) : 0u) +
+                          (st1 >= 4 && st1 < kNumSections ? 1u << (8 * (st1 - 4)) : 0u);
+      const unsigned clo = __reduce_add_sync(0xffffffffu, lo), chi = __reduce_add_sync(0xffffffffu, hi);
+      if ((clo | chi) == 0u) break;  // every slot is done
+      int sec = 0, best = (int)(clo & 255u);
 #pragma unroll
-      for (int q = 0; q < kNumSections; ++q) {
-        const unsigned m0 = __ballot_sync(0xffffffffu, st0 == q);
-        const unsigned m1 = __ballot_sync(0xffffffffu, st1 == q);
-        const int score = __popc(m0) + __popc(m1);
+      for (int q = 1; q < kNumSections; ++q) {
+        const int score = (int)(((q < 4 ? clo : chi) >> (8 * (q & 3))) & 255u);
         if (score > best) {
           best = score;
           sec = q;
-          sm0 = m0;
-          sm1 = m1;
         }
       }
-      if (sec < 0) {  // no slot in a section state (cannot happen): retire them rather than spin
-        if (st0 != kDone) U(F_META, g0) = kDone;
-        if (st1 != kDone) U(F_META, g1) = kDone;
-        __syncwarp();
-        continue;
-      }
+      const unsigned sm0 = __ballot_sync(0xffffffffu, st0 == sec);
+      const unsigned sm1 = __ballot_sync(0xffffffffu, st1 == sec);
       // ---- pack up to 32 slots in that state onto the lanes ----
       const unsigned below = (1u << lane_id) - 1u;
       const int n0 = __popc(sm0);
