@@ -57,6 +57,7 @@ struct PhantomParams {
   int n_mat, n_e;              // tables hold nodes E = 0 .. n_e - 1 keV
   int n_tab, e0;               // nodes staged per launch: E = e0 .. e0 + n_tab - 1 keV
   long long n_vox;
+  uint32_t m_nx, m_nxy;        // floor(2^32 / nx), floor(2^32 / (nx ny)) (2^32 - 1 for 1)
   float ox, oy, oz, inv_dx, inv_dy, inv_dz, dx, dy, dz;
   const float2* vox;           // {density, material id bits}
   const uint2* alias;          // per alias column {acceptance threshold on x >> 9, alias voxel}

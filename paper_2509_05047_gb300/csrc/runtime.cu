@@ -852,6 +852,9 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   jb.sc = sc->params;
   PhantomParams& q = jb.ph;
   q.nx = pd.nx;
+  q.m_nx = pd.nx > 1 ? (uint32_t)((1ull << 32) / (unsigned long long)pd.nx) : 0xffffffffu;
+  q.m_nxy = (long long)pd.nx * pd.ny > 1 ? (uint32_t)((1ull << 32) / ((unsigned long long)pd.nx * pd.ny))
+                                         : 0xffffffffu;
   q.ny = pd.ny;
   q.nz = pd.nz;
   q.n_mat = ph->n_mat;

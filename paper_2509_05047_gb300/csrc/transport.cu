@@ -389,7 +389,19 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
           const uint2 at = __ldg(ph.alias + col);
           const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
-          const int ix = v % ph.nx, iy = (v / ph.nx) % ph.ny, iz = v / (ph.nx * ph.ny);
+          // v = (iz ny + iy) nx + ix: quotients from a multiply-high with floor(2^32 / d),
+          // at most one below the true quotient, then one correction
+          const unsigned nxy = (unsigned)(ph.nx * ph.ny);
+          unsigned iz = __umulhi((unsigned)v, ph.m_nxy), rem = (unsigned)v - iz * nxy;
+          if (rem >= nxy) {
+            ++iz;
+            rem -= nxy;
+          }
+          unsigned iy = __umulhi(rem, ph.m_nx), ix = rem - iy * (unsigned)ph.nx;
+          if (ix >= (unsigned)ph.nx) {
+            ++iy;
+            ix -= (unsigned)ph.nx;
+          }
           const float ex = ph.ox + ((float)ix + uni(2)) * ph.dx, ey = ph.oy + ((float)iy + uni(3)) * ph.dy,
                       ez = ph.oz + ((float)iz + uni(4)) * ph.dz;
           const float ct = 2.0f * uni(5) - 1.0f;
