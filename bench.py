@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--e-res", type=float, default=0.0,
                     help="energy resolution FWHM at 511 keV (fraction); the no-LUT mode uses 0.112 "
                          "with the small configuration's 425-650 keV window")
+    ap.add_argument("--lut-axes", default="full", choices=["full", "e", "eab", "etz"],
+                    help="LUT axes kept (Sec. 2.2.2's lower-dimensional LUTs, from synthetic histograms): "
+                         "e energy, ab incidence angles, tz crystal positions")
     ap.add_argument("--gaps", type=int, default=0, choices=[0, 1, 2],
                     help="gaps between modules and blocks: 1 loses photons in a gap, 2 assigns them "
                          "to edge crystals (paper-scale workload; 2 mm gaps, 18 x 55 LUT positions)")
@@ -277,11 +280,18 @@ def workload_inputs(a):
     sc, mats, ph, lut, sens = build_inputs(a.rings, a.tof_bins, a.workload, a.gaps)
     if a.e_res > 0:
         sc.e_res = a.e_res
+    keep = {"e": ("e",), "eab": ("e", "a", "b"), "etz": ("e", "t", "z")}.get(a.lut_axes)
+    if keep is not None:
+        inc, det = W.lut_histograms(lut, counts=50.0)
+        lut = W.lut_reduced(lut, inc, det, keep)
     base_wl = WORKLOAD_SMALL if a.workload == "small" else WORKLOAD
     workload = base_wl if not (a.rings or a.tof_bins) else \
         f"profiling case: {base_wl} with {sc.n_rings} rings and {sc.n_tof} TOF bins"
     if a.e_res > 0:
         workload += f", energy resolution {100 * a.e_res:.1f} % FWHM at 511 keV"
+    if keep is not None:
+        workload += (f", lower-dimensional LUT {lut.n_e}x{lut.n_a}x{lut.n_b}x{lut.n_tpos}x{lut.n_apos} "
+                     f"(axes kept: {'+'.join(keep)})")
     if a.gaps:
         workload += (f", {sc.gap_t:g} mm module and {sc.gap_a:g} mm block gaps with LUT positions "
                      f"{sc.n_tpos}x{sc.n_apos}, "
