@@ -75,4 +75,7 @@ def test_compton_photons_are_dropped_only_five_sigma_below_the_window():
     assert np.all(e[st == oracle.DETECTED] >= cut)
     dropped = (st == oracle.ENERGY_WINDOW) & (e < cut)
     assert dropped.sum() > 100
+    # photons ended in transport (no hit on the cylinder) are all below the cut
+    in_transport = (st == oracle.ENERGY_WINDOW) & np.all(rec["hit"].reshape(-1, 3) == 0.0, axis=1)
+    assert in_transport.sum() > 100 and np.all(e[in_transport] < cut)
     assert np.any((st != oracle.ENERGY_WINDOW) & (e >= cut) & (e < 425.0))

@@ -121,7 +121,8 @@ def test_gap_photons_are_lost_or_assigned_to_edge_crystals():
     for k in range(2):
         for i in np.flatnonzero(det1[:, k])[:3000]:
             assert oracle.place(sc, r1["hit"][i, k])[0] == 0
-    p_neg, neg = [], []
+    p_neg, neg, pa_low, low = [], [], [], []
+    n_blk = sc.n_rings // sc.module_a
     for i in np.flatnonzero(det2[:, 0])[:20000]:
         fl, tp, ap, cr, rg, xt, xa, bt, ba = oracle.place(sc, r2["hit"][i, 0])
         assert abs(r2["prob"][i, 0] - tpos_val[tp]) < 1e-6
@@ -130,7 +131,24 @@ def test_gap_photons_are_lost_or_assigned_to_edge_crystals():
             assert r2["crystal"][i, 0] in (left, right)
             p_neg.append(oracle.edge_prob(sc, xt, r2["alpha"][i, 0], sc.gap_t))
             neg.append(r2["crystal"][i, 0] == left)
-    p_neg, neg = np.array(p_neg), np.array(neg)
-    assert p_neg.size > 200
-    var = (p_neg * (1 - p_neg)).sum()
-    assert abs(neg.sum() - p_neg.sum()) < 4 * math.sqrt(var) + 1
+        if fl & 2:
+            ring = r2["ring"][i, 0]
+            if ba == 0:
+                assert ring == 0
+            elif ba == n_blk:
+                assert ring == sc.n_rings - 1
+            else:  # an inner block gap: one of its two edge rings, the lower with p1
+                assert ring in (ba * sc.module_a - 1, ba * sc.module_a)
+                pa_low.append(oracle.edge_prob(sc, xa, r2["beta"][i, 0], sc.gap_a))
+                low.append(ring == ba * sc.module_a - 1)
+    for p, hit in ((p_neg, neg), (pa_low, low)):
+        p, hit = np.array(p), np.array(hit, dtype=np.float64)
+        assert p.size > 200
+        var = (p * (1 - p)).sum()
+        assert abs(hit.sum() - p.sum()) < 4 * math.sqrt(var) + 1
+        # each photon follows its own probability: the residuals do not correlate with
+        # 2p - 1 (swapping the two edges would give a sum of -(2p - 1)^2)
+        c = 2 * p - 1
+        z = ((hit - p) * c).sum()
+        assert abs(z) < 4 * math.sqrt((p * (1 - p) * c * c).sum()) + 1
+        assert (c * c).sum() > 8 * math.sqrt((p * (1 - p) * c * c).sum()) + 8
