@@ -323,8 +323,15 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     start(g1);
     __syncwarp();
 
-    // words a section reads, one nibble per section: 7, 2, 4, 3, 0, 2
+    // words a section reads, one nibble per section: 7, 2, 4, 3, 0, 2.  After a refill
+    // the window holds words [4 nb - kRingWords, 4 nb) with 4 nb < k + need + 4, so it
+    // still holds word k only for need <= kRingWords - 3; EMIT (7) starts at k = 0.
+    // Detection reads at most 4 (energy blur 2, edge draws 2).
     constexpr uint32_t kNeedNibbles = 0x203427u;
+    static_assert(((kNeedNibbles >> 4) & 15u) <= kRingWords - 3 && ((kNeedNibbles >> 8) & 15u) <= kRingWords - 3 &&
+                      ((kNeedNibbles >> 12) & 15u) <= kRingWords - 3 && ((kNeedNibbles >> 20) & 15u) <= kRingWords - 3 &&
+                      4 <= kRingWords - 3 && (kNeedNibbles & 15u) <= kRingWords,
+                  "a section's words must fit the Philox window");
 
     for (;;) {
       const int st0 = (int)(U(F_META, g0) & 7u), st1 = (int)(U(F_META, g1) & 7u);
