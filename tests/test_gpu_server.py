@@ -10,13 +10,15 @@ pytestmark = pytest.mark.gpu
 
 
 class World:
-    def __init__(self, budget=0):
+    def __init__(self, budget=0, gaps=0):
         import torch
         from paper_2509_05047_gb300 import build
         build.build()
         self.torch = torch
         self.ctx = psc.psc_create(0, budget)
         self.sc = W.scanner_tiny()
+        if gaps:  # 72 modules of 4 crystals, 4 blocks of 4 rings, 1 mm gaps
+            self.sc.gap_mode, self.sc.gap_t, self.sc.gap_a = gaps, 1.0, 1.0
         self.s = psc.psc_load_scanner(self.ctx, psc.scanner_desc(self.sc))
         m = psc.psc_load_materials(self.ctx, psc.materials_desc(W.standard_materials()).desc)
         self.phantoms = [W.phantom_water_cylinder(),
@@ -83,11 +85,14 @@ def _requests(world):
     ]
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("gaps", [0, 2])
+def test_served_results_equal_alone(gaps):
+    """Also on a scanner with gaps (edge-crystal assignment, LUT positions of
+    the virtual crystals): the batched launches carry each job's scanner."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    w = World()
+    w = World(gaps=gaps)
     try:
         reqs = _requests(w)
         ref = w.alone(reqs)
