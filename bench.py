@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--gaps", type=int, default=0, choices=[0, 1, 2],
                     help="gaps between modules and blocks: 1 loses photons in a gap, 2 assigns them "
                          "to edge crystals (paper-scale workload; 2 mm gaps, 18 x 55 LUT positions)")
+    ap.add_argument("--sigma", type=float, nargs=3, default=[2.0, 2.0, 2.0],
+                    help="precision study: smoothing sigma in bins (radial, view, axial); the paper's "
+                         "kernel widths, FWHM 10 / 5 / 18 bins, are 4.25 2.12 7.64")
     ap.add_argument("--reference-histories", type=float, default=1e10,
                     help="precision study: histories of the FP32 reference estimate")
     ap.add_argument("--precision-workload", default="small", choices=["small", "paper"],
@@ -550,7 +553,7 @@ def run_precision(a):
     sn_id = psc.psc_load_sinogram(ctx, s_id, sens, per_lor=True)
     a_id = psc.psc_acc_create(ctx, s_id)
     sh = torch.cuda.current_stream(dev).cuda_stream
-    sigma = (2.0, 2.0, 2.0)
+    sigma = tuple(a.sigma)
 
     def estimate(n, lut_id, seed, out):
         psc.psc_acc_zero(ctx, a_id, sh)
