@@ -17,7 +17,10 @@
 // twice as many slots as lanes the chosen section usually fills the warp,
 // where one history per lane left most lanes idle (the states of 32
 // histories spread over six sections).  The code holds a single copy of each
-// section, and one rejection-sampling try runs per iteration.
+// section, and one rejection-sampling try runs per iteration.  Pools stay
+// per warp, so warps never wait on each other: pools shared by two warps
+// (barrier-coupled) and larger pools (fewer resident warps) both measured
+// slower on this issue-bound loop.
 //
 // Random numbers: a history's sub-streams (0: emission + TOF blur, 1: photon
 // A, 2: photon B) are read through an 8-word window per slot; the only
