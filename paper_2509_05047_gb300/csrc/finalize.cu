@@ -36,6 +36,9 @@
 namespace psc {
 
 constexpr int NB = 8;            // outputs per window step along the smoothed axis
+// wide windows (radius 16 and up) take half the step: fewer registers, more warps
+template <int KT>
+constexpr int kNb = KT >= 16 ? 4 : NB;
 constexpr int kSmoothThreads = 256;
 
 // half-sample symmetric reflection of row m into [0, n), periodic beyond
@@ -202,6 +205,7 @@ using Weights = float[2 * kMaxSmoothRadius + 1];
 template <int KT, class In, class Cvt, class Store>
 __device__ __forceinline__ void slide(const In* __restrict__ src, long long stride, int n, const Weights& g,
                                       Cvt cvt, Store store) {
+  constexpr int NB = kNb<KT>;
   float w[NB + 2 * KT];
 #pragma unroll
   for (int j = 0; j < 2 * KT; ++j) {
@@ -272,6 +276,7 @@ __device__ __forceinline__ void slide_any(const In* src, long long stride, int n
 // ---------------------------------------------------------------------------
 template <int KT>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __grid_constant__ FinParams P) {
+  constexpr int NB = kNb<KT>;
   const int VT = P.V * P.T;
   const int c = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (c >= VT) return;
@@ -305,6 +310,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
 // ---------------------------------------------------------------------------
 template <int KT>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __grid_constant__ FinParams P) {
+  constexpr int NB = kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
@@ -330,6 +336,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // 0 where the input is 0 (the smoothing-normalisation sinogram)
 template <int KT, bool kDivide>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
+  constexpr int NB = kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
