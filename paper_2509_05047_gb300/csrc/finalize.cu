@@ -202,10 +202,10 @@ __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 using Weights = float[2 * kMaxSmoothRadius + 1];
 
-template <int KT, class In, class Cvt, class Store>
+template <int KT, int NBS, class In, class Cvt, class Store>
 __device__ __forceinline__ void slide(const In* __restrict__ src, long long stride, int n, const Weights& g,
                                       Cvt cvt, Store store) {
-  constexpr int NB = kNb<KT>;
+  constexpr int NB = NBS;
   float w[NB + 2 * KT];
 #pragma unroll
   for (int j = 0; j < 2 * KT; ++j) {
@@ -262,10 +262,10 @@ __device__ __forceinline__ void slide_generic(const In* __restrict__ src, long l
   }
 }
 
-template <int KT, class In, class Cvt, class Store>
+template <int KT, int NBS = kNb<KT>, class In, class Cvt, class Store>
 __device__ __forceinline__ void slide_any(const In* src, long long stride, int n, int K, const Weights& g, Cvt cvt,
                                           Store store) {
-  if constexpr (KT >= 0) slide<KT>(src, stride, n, g, cvt, store);
+  if constexpr (KT >= 0) slide<KT, NBS>(src, stride, n, g, cvt, store);
   else slide_generic(src, stride, n, K, g, cvt, store);
 }
 
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // 0 where the input is 0 (the smoothing-normalisation sinogram)
 template <int KT, bool kDivide>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
-  constexpr int NB = kNb<KT>;
+  constexpr int NB = KT >= 0 ? 4 : kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
       P.out[b0 + q * bin_step] = f32_to_f64(y);
     }
   };
-  slide_any<KT>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
+  slide_any<KT, NB>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
 }
 
 // reciprocal of a normalisation sinogram, 0 where it is 0: FP64 (r) and/or
