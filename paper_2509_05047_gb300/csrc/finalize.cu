@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
 // ---------------------------------------------------------------------------
 template <int KT>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __grid_constant__ FinParams P) {
-  constexpr int NB = kNb<KT>;
+  constexpr int NB = KT >= 0 && KT < 16 ? 12 : kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
     for (int q = 0; q < NB; ++q)
       if (v0 + q < V) dst[(v0 + q) * I] = y[q];
   };
-  slide_any<KT>(src, I, V, P.K[1], P.g[1], cvt, store);
+  slide_any<KT, NB>(src, I, V, P.K[1], P.g[1], cvt, store);
 }
 
 // ---------------------------------------------------------------------------
