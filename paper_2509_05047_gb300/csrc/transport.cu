@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         // ---- emission (stream 0, words 0..6) ----
         if (sec == kEmit) {
           const uint32_t w0 = word(0), w1 = word(1);
-          const long long col = (long long)(((unsigned long long)w0 * (unsigned long long)ph.n_vox) >> 32);
+          const unsigned col = __umulhi(w0, (unsigned)ph.n_vox);  // n_vox < 2^31
           const uint2 at = __ldg(ph.alias + col);
           const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
           // v = (iz ny + iy) nx + ix: quotients from a multiply-high with floor(2^32 / d),
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
                 setF(F_PZ, g, qz);
                 setF(F_PATH, g, Fv(F_PATH, g) + dist);
                 U(F_CNT, g) = cnt + 1u;
-                const float2 vx = __ldg(ph.vox + ((long long)iz * ph.ny + iy) * ph.nx + ix);
+                const float2 vx = __ldg(ph.vox + (unsigned)((iz * ph.ny + iy) * ph.nx + ix));  // n_vox < 2^31
                 const int mat = __float_as_int(vx.y);
                 const float4 cum = interp_xs(s_xs + mat * ph.n_tab, ph.n_tab, ph.e0, e);
                 const float t = uni(k) * mu_max;
