@@ -212,8 +212,12 @@ __device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alph
 
 
 // kDebug: statistics counters and per-history listmode outputs are compiled
-// in only when a launch asks for them, so the production loop stays small
-template <int DT, bool kDebug>
+// in only when a launch asks for them, so the production loop stays small.
+// kOneJob (production launches of a single job with an f32 LUT, the common
+// case): the sections read the job's parameters straight from the kernel
+// parameter space, where they are instruction operands, instead of from the
+// shared-memory copy that multi-job launches stage per chunk.
+template <int DT, bool kDebug, bool kOneJob = false>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant__ BatchParams B) {
   extern __shared__ float4 smem[];
   const unsigned tid = threadIdx.x, bdim = blockDim.x;
@@ -280,7 +284,10 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     }
     __syncthreads();
 
-    const Job& J = s_job;
+    const Job& J = [&]() -> const Job& {
+      if constexpr (kOneJob) return B.jobs[0];
+      else return s_job;
+    }();
     const PhantomParams& ph = J.ph;
     const ScannerParams& S = J.sc;
     const float* s_maj = reinterpret_cast<const float*>(s_xs + ph.n_mat * ph.n_tab);
@@ -778,12 +785,12 @@ size_t transport_smem_bytes(const PhantomParams& ph, int block) {
          sizeof(float4) * (size_t)ph.n_mat * ph.n_tab + sizeof(float) * (ph.n_tab + kMaxMaterials);
 }
 
-template <int DT, bool kDebug>
+template <int DT, bool kDebug, bool kOneJob = false>
 static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT, kDebug>,
+  cudaError_t e = cudaFuncSetAttribute(transport_kernel<DT, kDebug, kOneJob>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  transport_kernel<DT, kDebug><<<grid, block, smem, s>>>(p);
+  transport_kernel<DT, kDebug, kOneJob><<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -792,7 +799,11 @@ static cudaError_t launch_dt(const BatchParams& p, int grid, int block, size_t s
   bool debug = p.stats != nullptr;
   for (int j = 0; j < p.n_jobs; ++j)
     debug |= p.jobs[j].cls_out || p.jobs[j].key_out || p.jobs[j].q_out || p.lm[j].out;
-  return debug ? launch_dt<DT, true>(p, grid, block, smem, s) : launch_dt<DT, false>(p, grid, block, smem, s);
+  if (debug) return launch_dt<DT, true>(p, grid, block, smem, s);
+  if constexpr (DT == 0) {
+    if (p.n_jobs == 1) return launch_dt<0, false, true>(p, grid, block, smem, s);
+  }
+  return launch_dt<DT, false>(p, grid, block, smem, s);
 }
 
 cudaError_t launch_transport(const BatchParams& p, int lut_dtype, int grid, int block, size_t smem,

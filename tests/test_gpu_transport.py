@@ -487,3 +487,23 @@ def test_listmode_capacity_counts_beyond_the_buffer(tiny):
     with pytest.raises(psc.PscError) as e:
         psc.psc_simulate(tiny.ctx, bad, stream=tiny.stream())
     assert e.value.code == psc.PSC_EINVAL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "none"])
+def test_production_kernel_equals_debug_kernel(tiny, dtype):
+    """The production instantiations (no counters, no listmode; a single f32
+    job reads its parameters from the kernel parameters) add exactly the
+    accumulator of the instantiation the parity tests check."""
+    dts = {"f32": psc.PSC_LUT_F32, "f16": psc.PSC_LUT_F16, "bf16": psc.PSC_LUT_BF16}
+    lut = psc.psc_load_lut(tiny.ctx, psc.lut_desc(tiny.lut, dts[dtype]).desc) if dtype in dts else 0
+    n = 300_000
+    tiny.zero()
+    tiny.run(SEED + 61, 0, n, listmode=False, lut=lut, stats=True)
+    debug = tiny.acc().clone()
+    tiny.zero()
+    tiny.run(SEED + 61, 0, n, listmode=False, lut=lut, stats=False)
+    prod = tiny.acc()
+    assert int(debug.sum()) > 0
+    assert bool((prod == debug).all())
+    if lut:
+        psc.psc_unload(tiny.ctx, lut)
