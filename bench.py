@@ -192,7 +192,7 @@ OPS_PER_HISTORY = 60
 # folded to one bin (the full 43.8 GB accumulator is too large to capture);
 # the traffic is the binned atomics and LUT misses, so it scales with the
 # histories of a launch
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.60e6 + 25.48e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.44e6 + 24.65e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
 # algorithmic HBM bytes per bin of the smoothing finalize: radial 8 + 4,
 # view 4 + 4, axial 4 + 8 (per-LOR sensitivity reads are 8 / n_tof more)
 FINALIZE_BYTES_PER_BIN = 32
@@ -445,7 +445,7 @@ def run_native(a):
     roofline = {"bound": "alu", "achieved": round(achieved / 1e9, 1), "peak": round(peak_ops / 1e9, 1),
                 "unit": "Gop/s", "frac": round(achieved / peak_ops, 4),
                 "traffic": int(TRANSPORT_DRAM_BYTES_PER_HISTORY * n),
-                "kernel": "psc::transport_kernel<0, false>", "kernel_ms": round(kern_ms, 3),
+                "kernel": "psc::transport_kernel<0, false, true, true>", "kernel_ms": round(kern_ms, 3),
                 "peak_source": f"152 SMs x 128 lanes x median SM clock under load ({sm_mhz:.0f} MHz)"}
     # the three smoothing passes together, against the measured copy bandwidth
     fin_gbs = FINALIZE_BYTES_PER_BIN * sc.n_bins / (phase[2] / 1e3) / 1e9
