@@ -72,6 +72,13 @@ __host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
 }
 
 
+// per-half maximum of two pairs of unsigned 16-bit values
+__device__ __forceinline__ unsigned umax16x2(unsigned a, unsigned b) {
+  unsigned d;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
 __device__ __forceinline__ float interp_scalar(const float* t, int n_tab, int e0, float e) {
   const float fe = e - (float)e0;
   const int i = max(0, min((int)fe, n_tab - 2));
@@ -357,15 +364,14 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
                           (st1 >= 4 && st1 < kNumSections ? 1u << (8 * (st1 - 4)) : 0u);
       const unsigned clo = __reduce_add_sync(0xffffffffu, lo), chi = __reduce_add_sync(0xffffffffu, hi);
       if ((clo | chi) == 0u) break;  // every slot is done
-      int sec = 0, best = (int)(clo & 255u);
-#pragma unroll
-      for (int q = 1; q < kNumSections; ++q) {
-        const int score = (int)(((q < 4 ? clo : chi) >> (8 * (q & 3))) & 255u);
-        if (score > best) {
-          best = score;
-          sec = q;
-        }
-      }
+      // the most-populated section, the lowest on a tie: keys count << 3 | (7 - q)
+      // in 16-bit halves, two paired maxima, then the larger half.  A section
+      // with slots outranks every empty one (key >= 8), so sec is never empty.
+      const unsigned k01 = __byte_perm(clo, 0u, 0x4140) * 8u + 0x00060007u;
+      const unsigned k23 = __byte_perm(clo, 0u, 0x4342) * 8u + 0x00040005u;
+      const unsigned k45 = __byte_perm(chi, 0u, 0x4140) * 8u + 0x00020003u;
+      const unsigned km = umax16x2(umax16x2(k01, k23), k45);
+      const int sec = 7 - (int)(max(km & 0xffffu, km >> 16) & 7u);
       const unsigned sm0 = __ballot_sync(0xffffffffu, st0 == sec);
       const unsigned sm1 = __ballot_sync(0xffffffffu, st1 == sec);
       // ---- pack up to 32 slots in that state onto the lanes ----
