@@ -72,6 +72,13 @@ __host__ __device__ constexpr uint32_t meta(int state, int photon, int stream) {
 }
 
 
+// 1 << s, and 0 for s >= 32 (the PTX shift clamps its amount to the width)
+__device__ __forceinline__ unsigned shl_or_zero(unsigned s) {
+  unsigned d;
+  asm("shl.b32 %0, %1, %2;" : "=r"(d) : "r"(1u), "r"(s));
+  return d;
+}
+
 // per-half maximum of two pairs of unsigned 16-bit values
 __device__ __forceinline__ unsigned umax16x2(unsigned a, unsigned b) {
   unsigned d;
@@ -357,13 +364,14 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
       const int st0 = (int)(U(F_META, g0) & 7u), st1 = (int)(U(F_META, g1) & 7u);
 
       // ---- warp vote: the section that the most slots wait for ----
-      // slot counts per section, one byte each (at most 64 slots): sections
-      // 0..3 in lo, 4..5 in hi, summed over the warp by two reductions
-      const unsigned lo = (st0 < 4 ? 1u << (8 * st0) : 0u) + (st1 < 4 ? 1u << (8 * st1) : 0u);
-      const unsigned hi = (st0 >= 4 && st0 < kNumSections ? 1u << (8 * (st0 - 4)) : 0u) +
-                          (st1 >= 4 && st1 < kNumSections ? 1u << (8 * (st1 - 4)) : 0u);
+      // slot counts per state, one byte each (at most 64 slots): states 0..3
+      // in lo, 4..7 in hi (sections 4, 5 in its bytes 0, 1), summed over the
+      // warp by two reductions.  A state's bit is 1 << 8 st, or 1 << (8 st - 32)
+      // in hi, where shift amounts of 32 and more (unsigned wrap included) give 0.
+      const unsigned lo = shl_or_zero(8u * st0) + shl_or_zero(8u * st1);
+      const unsigned hi = shl_or_zero(8u * st0 - 32u) + shl_or_zero(8u * st1 - 32u);
       const unsigned clo = __reduce_add_sync(0xffffffffu, lo), chi = __reduce_add_sync(0xffffffffu, hi);
-      if ((clo | chi) == 0u) break;  // every slot is done
+      if ((clo | (chi & 0xffffu)) == 0u) break;  // every slot is done
       // the most-populated section, the lowest on a tie: keys count << 3 | (7 - q)
       // in 16-bit halves, two paired maxima, then the larger half.  A section
       // with slots outranks every empty one (key >= 8), so sec is never empty.
