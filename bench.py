@@ -192,7 +192,7 @@ OPS_PER_HISTORY = 60
 # folded to one bin (the full 43.8 GB accumulator is too large to capture);
 # the traffic is the binned atomics and LUT misses, so it scales with the
 # histories of a launch
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (114.35e6 + 24.73e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.56e6 + 24.24e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
 # algorithmic HBM bytes per bin of the smoothing finalize: radial 8 + 4,
 # view 4 + 4, axial 4 + 8 (per-LOR sensitivity reads are 8 / n_tof more)
 FINALIZE_BYTES_PER_BIN = 32
