@@ -203,6 +203,11 @@ typedef struct {
   double sigma[3];                 /* Gaussian sigma in bins: radial, view, axial (within segment) */
   double scale;                    /* global factor (e.g. 1/histories, decay, Sec. 2.4.3) */
   int32_t sens_first;              /* 0 (paper order): smooth, then x sens; 1: x sens, then smooth */
+  int32_t seg_lo, seg_hi;          /* finalize only the planes of ring-difference segments [seg_lo,
+                                      seg_hi), segment rb - ra + n_rings - 1 (smoothing never crosses
+                                      a segment, so each part is exact on its own; the output's other
+                                      planes are unspecified, since out also serves as working
+                                      memory); seg_lo == seg_hi: every plane */
 } psc_finalize_args;
 
 /* Context on one CUDA device.  mem_budget_bytes bounds the device memory of
@@ -243,6 +248,14 @@ int psc_load_sinogram(psc_ctx* ctx, int32_t scanner, const double* host, int32_t
 /* int64 fixed-point accumulator sinogram (weight w adds rint(w * 2^32)). */
 int psc_acc_create(psc_ctx* ctx, int32_t scanner, int32_t* id);
 int psc_acc_zero(psc_ctx* ctx, int32_t acc, psc_stream stream);
+/* An accumulator in caller-owned device memory (int64, the scanner's
+ * sinogram size, 8-byte aligned, on the context's device): the context uses
+ * it like one of psc_acc_create (simulate into it, finalize it) but neither
+ * zeroes nor frees it, and it does not count against the memory budget.
+ * For callers that exchange accumulators themselves, e.g. the sum over the
+ * ranks that simulate parts of one request's histories, without a copy.
+ * The memory must stay valid until psc_unload of the id. */
+int psc_acc_wrap(psc_ctx* ctx, int32_t scanner, int64_t* device, int32_t* id);
 /* Copy the raw accumulator out / in (checkpoint and resume): device int64
  * arrays of the scanner's sinogram size. */
 int psc_acc_read(psc_ctx* ctx, int32_t acc, int64_t* out /* device */, psc_stream stream);
@@ -259,6 +272,28 @@ int psc_simulate(psc_ctx* ctx, const psc_sim_args* args, psc_stats* stats, psc_s
  * over the batch. */
 int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
                        psc_stream stream);
+/* Launch schedule of a batched transport launch. */
+typedef struct {
+  int32_t block;            /* threads per CTA */
+  int32_t grid;             /* CTAs (0: as many as fit on the device) */
+  int32_t chunks_per_cta;   /* work items per CTA and request */
+  int32_t max_chunk;        /* histories per work item at most */
+  double rate;              /* histories/s this schedule reached in the probes */
+  int32_t probed;           /* schedules timed by this call (0: the choice was cached) */
+} psc_schedule;
+/* psc_simulate_batch with a launch schedule picked by timed probes (no
+ * counterpart in the paper): a few candidate schedules (CTA size, work items
+ * per CTA, largest work item) each run the next slice of every request's
+ * histories (1/48 of each budget), and the fastest runs the rest.  Every
+ * history is simulated exactly once into its request's accumulator and
+ * accumulators do not depend on the schedule, so the result equals
+ * psc_simulate_batch's bit for bit.  The choice is cached per request mix
+ * (the requests' scanner, phantom and LUT objects), so later calls on the
+ * mix skip the probes.  The probes wait for the stream (host-side).  No
+ * per-history outputs (cls_out, key_out, q_out, lm_out): PSC_EINVAL.
+ * chosen (may be NULL) receives the schedule. */
+int psc_simulate_batch_tuned(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_schedule* chosen,
+                             psc_stream stream);
 /* Scatter estimate = acc * scale * 2^-32, [x norm -> smooth -> / norm],
  * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size).
  * With smoothing, out also serves as the first pass's FP32 working buffer
@@ -266,6 +301,23 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
  * and (2 n_rings - 1) * n_crystals / 2 <= 65535, else PSC_EINVAL. */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
+/* The scatter estimate of psc_finalize delivered to host memory (the
+ * end-to-end form for a caller that takes the estimate out of the device,
+ * e.g. to hand it to a reconstruction on the host).  work: device f64 of
+ * the scanner's sinogram size, holding the estimate (and the smoothing's
+ * first FP32 pass) as psc_finalize's out does; out_host: host f64 of the
+ * same size, best page-locked (psc_host_alloc gives the host link's rate).
+ * The estimate is computed in parts (plane ranges without smoothing; the
+ * axial pass in groups of whole ring-difference segments with it), and each
+ * part is copied to out_host on copy_stream as soon as it is written, so
+ * the transfer overlaps the rest of the finalize.  Kernels are enqueued on
+ * stream; copy_stream (may be the same stream) waits for each part and
+ * copies it: when copy_stream has reached the end of this call's work,
+ * out_host holds the estimate.  work must not be overwritten before then
+ * (order the next writer after an event on copy_stream).  Errors as
+ * psc_finalize, and PSC_EINVAL for a NULL out_host. */
+int psc_finalize_host(psc_ctx* ctx, const psc_finalize_args* args, double* work /* device */,
+                      double* out_host /* host */, psc_stream stream, psc_stream copy_stream);
 /* Smoothing-normalisation sinogram (Sec. 2.3.2: a heavily smoothed copy of
  * a sinogram divided by the sinogram itself, made once from the simulation
  * of a large cylinder): out[bin] = smooth(acc)[bin] / acc[bin], 0 where
@@ -298,18 +350,28 @@ int psc_acc_rotate_sum(psc_ctx* ctx, int32_t acc, int32_t step, int32_t out_acc,
  * capped, or must not be allocated once a real-time loop is running).  The
  * paper has no counterpart.  Inputs and the output are the caller's device
  * arrays: acc int64 and out f64 of n_rings^2 x (n_crystals/2) x n_rad x
- * n_tof bins; sens / norm (NULL = none) per LOR when *_per_lor, else per
- * bin; sigma (host [3], NULL = no smoothing), scale and sens_first as in
+ * n_tof bins (n_crystals even, n_rad in [1, n_crystals - 1] with
+ * n_crystals - 1 - n_rad even, as for psc_load_scanner; else PSC_EINVAL);
+ * sens / norm (NULL = none) per LOR when *_per_lor, else per bin; sigma
+ * (host [3], NULL = no smoothing), scale and sens_first as in
  * psc_finalize_args.  The smoothing's working memory is one static device
- * array of 64 MiB per GPU (held from library load until process exit):
- * sinograms needing more than 4 bytes per bin plus 8 per normalisation
- * value (256-byte aligned) are rejected with PSC_EOVERFLOW.  No cudaMalloc,
- * cudaFree or allocating library call is made.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture.  All calls on a device share the
- * array and every call overwrites all of it that it reads, so nothing
- * needs clearing; calls that overlap on the GPU (other streams, other
- * threads) race on it and must be ordered by the caller. */
+ * array of 64 MiB per GPU: sinograms needing more than 4 bytes per bin plus
+ * 8 per normalisation value (256-byte aligned) are rejected with
+ * PSC_EOVERFLOW.  The calls make no cudaMalloc, cudaFree or allocating
+ * library call.  The array lives in this library's image, and with CUDA's
+ * default lazy module loading it is mapped on a device when the first
+ * smoothing call on that device looks up its address
+ * (cudaGetSymbolAddress): that first call takes 64 MiB of device memory
+ * (plus the allocation granularity), later calls none, and the array stays
+ * until the process exits.  So make the first call before another
+ * allocator reserves the device's memory, or run with
+ * CUDA_MODULE_LOADING=EAGER (the array is then mapped with the context);
+ * it should also come before any stream capture.  The address is cached
+ * per device for the life of the process: a device reset (cudaDeviceReset)
+ * between calls is not supported.  All calls on a device share the array
+ * and every call overwrites all of it that it reads, so nothing needs
+ * clearing; calls that overlap on the GPU (other streams, other threads)
+ * race on it and must be ordered by the caller. */
 int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t n_crystals, int32_t n_rad,
                         int32_t n_tof, const double* sens, int32_t sens_per_lor,
                         const double* norm, int32_t norm_per_lor, const double* sigma,

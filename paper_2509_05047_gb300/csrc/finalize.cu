@@ -17,9 +17,10 @@
 //   A  radial: acc (int64) -> FP32, columns (plane, view, tof) along rad,
 //              into the first half of the output buffer (used as scratch)
 //   B  view:   that -> FP32 working sinogram, columns (plane, rad, tof)
-//   C  axial:  working sinogram -> epilogue (x 1/norm, x sens: factors
-//              rounded to FP32, product widened exactly to FP64) -> out,
-//              columns (segment, view, rad, tof) along the segment's planes
+//   C  axial:  working sinogram -> epilogue (the FP32 value widened exactly,
+//              x 1/norm, x sens in FP64, each product rounded to nearest)
+//              -> out, columns (segment, view, rad, tof) along the
+//              segment's planes
 // No pass writes what it reads.  Kernels are truncated at ceil(4 sigma) with
 // weights normalised to 1 and zero-padded to the instantiated radius KT
 // (exact for K <= 8, then 10, 12, 16, 20, 24; a per-tap loop beyond), so the
@@ -173,12 +174,65 @@ __device__ __forceinline__ double dmul(double a, double b) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
 }
 
+// (double)y * f, rounded to nearest even, for a float y and a double f: the
+// 24-bit by 53-bit significand product P in [2^75, 2^77) from two 32 x 32 ->
+// 64-bit products; P >> 13 (or >> 12 when P < 2^76) puts the leading bit at
+// bit 63, the 11 bits below the kept 53 decide the rounding with the sticky
+// bit of the rest, and the rounded significand (hidden bit included) is
+// added to the exponent field, so a rounding carry moves into the exponent
+// (and past the largest finite value to infinity) as IEEE rounding does.
+// Zero operands are handled inline; subnormal, infinite and NaN operands and
+// results outside the normal range go to the FP64 hardware.
+__device__ __forceinline__ double mul_f32_f64(float y, double f) {
+  const unsigned by = (unsigned)__float_as_int(y);
+  const unsigned long long uf = (unsigned long long)__double_as_longlong(f);
+  const unsigned fhi = (unsigned)(uf >> 32);
+  const unsigned ey = (by >> 23) & 0xffu, ef = (fhi >> 20) & 0x7ffu;
+  const unsigned long long sign = (unsigned long long)((by ^ fhi) & 0x80000000u) << 32;
+  if (((by << 1) == 0u && ef != 0x7ffu) || ((uf << 1) == 0ull && ey != 0xffu))
+    return __longlong_as_double((long long)sign);
+  if (ey - 1u >= 254u || ef - 1u >= 0x7feu) return hw_dmul(hw_f32_to_f64(y), f);
+  const unsigned my = (by & 0x7fffffu) | 0x800000u;
+  const unsigned long long t0 = (unsigned long long)my * (unsigned)uf;                      // < 2^56
+  const unsigned long long t1 = (unsigned long long)my * ((fhi & 0xfffffu) | 0x100000u);   // < 2^45
+  const unsigned long long hi = (t0 >> 13) + (t1 << 19);                                    // P >> 13
+  const unsigned top = (unsigned)(hi >> 63), sh = top ^ 1u;
+  const unsigned long long g = (hi << sh) | ((t0 >> 12) & (unsigned long long)sh);
+  const bool sticky = ((unsigned)t0 & (0x1fffu >> sh)) != 0u;
+  const unsigned long long q = g >> 11;
+  const unsigned rem = (unsigned)g & 0x7ffu;
+  const unsigned up = (rem > 0x400u || (rem == 0x400u && (sticky || (q & 1ull)))) ? 1u : 0u;
+  const int e = (int)ey - 127 + (int)ef + (int)top;  // (ey - 127) + (ef - 1023) + 1023, +1 when P >= 2^76
+  if (e <= 0 || e >= 0x7ff) return hw_dmul(hw_f32_to_f64(y), f);
+  return __longlong_as_double((long long)(sign | (((unsigned long long)(e - 1) << 52) + q + up)));
+}
+
+// The j-th plane a launch covers: plane j itself, or, when the launch is
+// restricted to ring-difference segments [seg_lo, seg_hi), the j-th plane of
+// those segments in segment order and, within a segment, by ring a (plane
+// ra (n_rings + 1) + d for d = s - n_rings + 1).  The host sizes the grid to
+// the planes of the range, so the walk ends inside it.
+__device__ __forceinline__ long long plane_at(const FinParams& P, long long j) {
+  if (P.seg_hi <= P.seg_lo) return j;
+  const int nr = P.n_rings;
+  int sg = P.seg_lo;
+  for (;;) {
+    const int L = nr - abs(sg - (nr - 1));
+    if (j < L || sg + 1 >= P.seg_hi) {
+      const int d = sg - (nr - 1);
+      return (long long)(max(0, -d) + (int)j) * (nr + 1) + d;
+    }
+    j -= L;
+    ++sg;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // no smoothing: out = (acc * c) * sens (FP64)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_constant__ FinParams P) {
   // grid.y = plane, grid.x strides over the plane's J = V * R * T bins
-  const long long plane = blockIdx.y;
+  const long long plane = plane_at(P, P.plane0 + (long long)blockIdx.y);
   const int J = P.V * P.R * P.T;
   const long long base = plane * J;
   const long long lor0 = plane * (long long)P.V * P.R;
@@ -281,7 +335,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
   const int c = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (c >= VT) return;
   const int v = (int)fdiv((unsigned)c, P.magic_T), t = c - v * P.T;
-  const long long line = (long long)blockIdx.y * P.V + v;
+  const long long line = plane_at(P, blockIdx.y) * P.V + v;
   const int R = P.R, T = P.T;
   const long long base = line * R * T + t;  // bin of (line, r = 0, t)
   const float cf = (float)P.c;
@@ -314,7 +368,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
-  const long long base = (long long)blockIdx.y * P.V * I + i;
+  const long long base = plane_at(P, blockIdx.y) * P.V * I + i;
   const float* src = reinterpret_cast<const float*>(P.out) + base;
   float* dst = P.scratch + base;
   auto cvt = [](float x, int) { return x; };
@@ -334,14 +388,17 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // ---------------------------------------------------------------------------
 // kDivide: the output is the smoothed value over the (scaled) input bin,
 // 0 where the input is 0 (the smoothing-normalisation sinogram)
-template <int KT, bool kDivide>
+// kNorm: a normalisation reciprocal multiplies the output (compiled in only
+// where there is one: its factors would otherwise hold registers)
+template <int KT, bool kDivide, bool kNorm>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
   constexpr int NB = KT >= 0 ? 4 : kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
   const int nr = P.n_rings;
-  const int seg = blockIdx.y / P.V, v = blockIdx.y - seg * P.V;
+  const int sl = blockIdx.y / P.V, v = blockIdx.y - sl * P.V;
+  const int seg = P.seg0 + sl;
   const int d = seg - (nr - 1);  // ring difference rb - ra
   const int ra0 = max(0, -d);
   const int L = nr - abs(d);
@@ -353,14 +410,15 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
   const long long lor0 = p0 * lors + (long long)v * P.R + fdiv((unsigned)i, P.magic_T);
   const long long lor_step = (long long)(nr + 1) * lors;
   auto cvt = [](float x, int) { return x; };
-  const bool use_rnorm = P.rnorm || P.rnorm32, use_sens = !P.sens_first && P.sens;
-  // the smoothed value carries FP32 precision: the factors are FP32 (rounded
-  // once), multiplied in FP32 and the result widened exactly to FP64.  The
-  // factor loads of a step are issued before any output is stored.
+  const bool use_sens = !P.sens_first && P.sens;
+  // the epilogue in FP64: the smoothed FP32 value widened exactly, times the
+  // FP64 reciprocal of the normalisation, times the FP64 sensitivity, each
+  // product rounded to nearest (on the integer pipes).  The factor loads of
+  // a step are issued before any output is stored.
   const float cf = (float)P.c;
   auto store = [&](int k0, const float (&o)[NB]) {
     const long long b0 = bin0 + k0 * bin_step, l0 = lor0 + k0 * lor_step;
-    float fr[NB], fs[NB];
+    double fr[kNorm ? NB : 1], fs[NB];
     long long qa[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -369,21 +427,26 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
       if (kDivide) {
         qa[q] = in ? __ldg(P.acc + bin) : 0;
       } else {
-        fr[q] = use_rnorm && in ? factor(P.rnorm32, P.rnorm, P.norm_per_lor ? lor : bin) : 1.0f;
-        fs[q] = use_sens && in ? factor(P.sens32, P.sens, P.sens_per_lor ? lor : bin) : 1.0f;
+        if constexpr (kNorm) fr[q] = in ? at(P.rnorm, P.norm_per_lor ? lor : bin) : 1.0;
+        fs[q] = use_sens && in ? at(P.sens, P.sens_per_lor ? lor : bin) : 1.0;
       }
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       if (k0 + q >= L) break;
-      float y = o[q];
+      const float y = o[q];
+      double x;
       if (kDivide) {
-        y = qa[q] != 0 ? y / (i64_to_f32(qa[q]) * cf) : 0.0f;
+        x = f32_to_f64(qa[q] != 0 ? y / (i64_to_f32(qa[q]) * cf) : 0.0f);
+      } else if (kNorm) {
+        x = mul_f32_f64(y, fr[kNorm ? q : 0]);
+        if (use_sens) x = dmul(x, fs[q]);
+      } else if (use_sens) {
+        x = mul_f32_f64(y, fs[q]);
       } else {
-        if (use_rnorm) y *= fr[q];
-        if (use_sens) y *= fs[q];
+        x = f32_to_f64(y);
       }
-      P.out[b0 + q * bin_step] = f32_to_f64(y);
+      P.out[b0 + q * bin_step] = x;
     }
   };
   slide_any<KT, NB>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
@@ -483,26 +546,55 @@ PSC_LAUNCHER(ViewL, smooth_view_kernel)
 template <int KT>
 struct AxialL {
   static cudaError_t run(const FinParams& p, dim3 grid, cudaStream_t s) {
-    if (p.divide_acc) smooth_axial_kernel<KT, true><<<grid, kSmoothThreads, 0, s>>>(p);
-    else smooth_axial_kernel<KT, false><<<grid, kSmoothThreads, 0, s>>>(p);
+    if (p.divide_acc) smooth_axial_kernel<KT, true, false><<<grid, kSmoothThreads, 0, s>>>(p);
+    else if (p.rnorm) smooth_axial_kernel<KT, false, true><<<grid, kSmoothThreads, 0, s>>>(p);
+    else smooth_axial_kernel<KT, false, false><<<grid, kSmoothThreads, 0, s>>>(p);
     return cudaGetLastError();
   }
 };
 
-cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s) {
+cudaError_t launch_finalize_planes(const FinParams& p, int lo, int hi, int sms, cudaStream_t s) {
+  if (hi <= lo) return cudaSuccess;
+  const long long J = (long long)p.V * p.R * p.T;
+  const long long n = hi - lo;
+  const long long per_plane = std::max(1LL, std::min((J + 255) / 256, 8LL * sms / n + 1));
+  FinParams q = p;
+  q.plane0 = lo;
+  finalize_plain_kernel<<<dim3((unsigned)per_plane, (unsigned)n), 256, 0, s>>>(q);
+  return cudaGetLastError();
+}
+
+static unsigned smooth_blocks(long long n) { return (unsigned)((n + kSmoothThreads - 1) / kSmoothThreads); }
+
+int finalize_planes(const FinParams& p) {
+  if (p.seg_hi <= p.seg_lo) return p.n_rings * p.n_rings;
+  int n = 0;
+  for (int sg = p.seg_lo; sg < p.seg_hi; ++sg) n += p.n_rings - std::abs(sg - (p.n_rings - 1));
+  return n;
+}
+
+cudaError_t launch_smooth_front(const FinParams& p, cudaStream_t s) {
   cudaError_t e;
-  const unsigned planes = (unsigned)((long long)p.n_rings * p.n_rings);
-  if (!p.smooth) {
-    const long long J = (long long)p.V * p.R * p.T;
-    const long long per_plane = std::max(1LL, std::min((J + 255) / 256, 8LL * sms / (long long)planes + 1));
-    finalize_plain_kernel<<<dim3((unsigned)per_plane, planes), 256, 0, s>>>(p);
-    return cudaGetLastError();
-  }
-  auto blocks = [](long long n) { return (unsigned)((n + kSmoothThreads - 1) / kSmoothThreads); };
+  const unsigned planes = (unsigned)finalize_planes(p);
   const long long I = (long long)p.R * p.T;
-  if ((e = dispatch_kt<RadialL>(p.KT[0], p, dim3(blocks((long long)p.V * p.T), planes), s)) != cudaSuccess) return e;
-  if ((e = dispatch_kt<ViewL>(p.KT[1], p, dim3(blocks(I), planes), s)) != cudaSuccess) return e;
-  return dispatch_kt<AxialL>(p.KT[2], p, dim3(blocks(I), (unsigned)((2LL * p.n_rings - 1) * p.V)), s);
+  if ((e = dispatch_kt<RadialL>(p.KT[0], p, dim3(smooth_blocks((long long)p.V * p.T), planes), s)) != cudaSuccess)
+    return e;
+  return dispatch_kt<ViewL>(p.KT[1], p, dim3(smooth_blocks(I), planes), s);
+}
+
+cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t s) {
+  if (hi <= lo) return cudaSuccess;
+  FinParams q = p;
+  q.seg0 = lo;
+  return dispatch_kt<AxialL>(p.KT[2], q, dim3(smooth_blocks((long long)p.R * p.T), (unsigned)((hi - lo) * p.V)), s);
+}
+
+cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s) {
+  if (!p.smooth) return launch_finalize_planes(p, 0, finalize_planes(p), sms, s);
+  cudaError_t e;
+  if ((e = launch_smooth_front(p, s)) != cudaSuccess) return e;
+  const bool all = p.seg_hi <= p.seg_lo;
+  return launch_smooth_axial(p, all ? 0 : p.seg_lo, all ? 2 * p.n_rings - 1 : p.seg_hi, s);
 }
 
 }  // namespace psc

@@ -41,9 +41,13 @@ extern "C" int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t 
                                    const double* sigma, double scale, int32_t sens_first,
                                    double* out, psc_stream stream) {
   if (!acc || !out) return psc_set_error(PSC_EINVAL, "acc and out must be device pointers");
+  // the sinogram shapes psc_load_scanner accepts: an even crystal count, the
+  // radial bins a centred clip of the n_crystals - 1 (same parity)
   if (n_crystals < 4 || (n_crystals & 1) || n_rings < 1 || n_tof < 1 || n_rad < 1 ||
-      n_rad > n_crystals - 1)
-    return psc_set_error(PSC_EINVAL, "bad sinogram dimensions");
+      n_rad > n_crystals - 1 || ((n_crystals - 1 - n_rad) & 1))
+    return psc_set_error(PSC_EINVAL,
+                         "bad sinogram dimensions (n_crystals even and >= 4, n_rings and n_tof >= 1, "
+                         "n_rad in [1, n_crystals - 1] with n_crystals - 1 - n_rad even)");
   if (!std::isfinite(scale)) return psc_set_error(PSC_EINVAL, "scale must be finite");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -91,7 +95,12 @@ extern "C" int psc_finalize_static(const int64_t* acc, int32_t n_rings, int32_t 
   }
 
   // set-up, once per device with that device current: the device address
-  // of the working array (its name in host code is only a host stand-in)
+  // of the working array (its name in host code is only a host stand-in).
+  // Under lazy module loading (CUDA's default) this lookup is also what
+  // loads this file's module and so maps the 64 MiB array on the device.
+  // The address is cached per device ordinal for the life of the process:
+  // a device reset (cudaDeviceReset) unloads the module and is not
+  // supported between calls.
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_setup_mu);

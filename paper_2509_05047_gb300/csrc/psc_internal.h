@@ -22,15 +22,17 @@ struct FinParams {
   float* scratch;              // FP32 working sinogram, n_bins floats (smoothing only)
   const double* sens;
   const double* norm;
-  const double* rnorm;         // 1/norm, 0 where norm == 0
-  const float* sens32;         // FP32 copies (round to nearest) of sens, norm and 1/norm, or
-  const float* norm32;         // nullptr: the smoothing then rounds the FP64 values itself
-  const float* rnorm32;
+  const double* rnorm;         // 1/norm (FP64), 0 where norm == 0: the smoothed epilogue's factor
+  const float* sens32;         // FP32 copies (round to nearest) of sens and norm for the radial
+  const float* norm32;         // pass, or nullptr: it then rounds the FP64 values itself
   int sens_per_lor, norm_per_lor;
   double c;                    // scale * 2^-32
   long long n_bins;
   int n_rings, V, R, T;
   int smooth, sens_first;
+  int plane0;                  // first plane (index into the launch's planes) of a plain launch
+  int seg0;                    // first ring-difference segment of an axial-pass launch
+  int seg_lo, seg_hi;          // finalize only the planes of segments [seg_lo, seg_hi); equal: all
   int divide_acc;              // output smoothed / (acc * c), 0 where acc == 0 (normalisation sinogram)
   unsigned magic_T;            // ceil(2^32 / T) for exact i / T, 0 when T == 1
   int K[3];                    // truncation radius per axis (radial, view, axial)
@@ -58,6 +60,14 @@ cudaError_t transport_occupancy(int lut_dtype, int block, size_t smem, int* bloc
 // or an error code with the message set
 int finalize_plan(FinParams& p, const double sigma[3]);
 cudaError_t launch_finalize(const FinParams& p, int sms, cudaStream_t s);
+// the parts of launch_finalize: the unsmoothed product over planes [lo, hi);
+// the radial and view passes over every plane; the axial pass (with the
+// epilogue) over ring-difference segments [lo, hi) (segment d + n_rings - 1)
+cudaError_t launch_finalize_planes(const FinParams& p, int lo, int hi, int sms, cudaStream_t s);
+// planes a finalize covers: all, or those of its segment range
+int finalize_planes(const FinParams& p);
+cudaError_t launch_smooth_front(const FinParams& p, cudaStream_t s);
+cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t s);
 // sinogram post-processing of int64 accumulators (postproc.cu)
 cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
                         cudaStream_t s);

@@ -1,6 +1,8 @@
 """GPU parity of the sinogram post-processing (sensitivity multiply and
 normalised separable smoothing) against the oracle, from synthetic
 accumulators written through the C ABI."""
+import math
+
 import numpy as np
 import pytest
 
@@ -77,8 +79,12 @@ def test_sensitivity_multiply_is_bit_exact(small, sens, scale):
     np.testing.assert_array_equal(out, exp)
 
 
-@pytest.mark.parametrize("sigma", [(2.0, 2.0, 2.0), (0.7, 3.3, 1.2), (9.0 / 2.3548, 6.0 / 2.3548, 10.5 / 2.3548),
-                                   (0.0, 1.0, 0.0)])
+# the last two: the paper's chosen FWHM [9, 6, 10.5] bins, and the widths
+# 4.25 / 2.12 / 7.64 of its upper bound (Sec. 2.3.2), whose axial radius
+# ceil(4 x 7.64) = 31 exceeds the largest instantiated window (24) and takes
+# the per-tap path, on segments shorter than the kernel
+@pytest.mark.parametrize("sigma", [(2.0, 2.0, 2.0), (0.7, 3.3, 1.2), (0.0, 1.0, 0.0),
+                                   (9.0 / 2.3548, 6.0 / 2.3548, 10.5 / 2.3548), (4.25, 2.12, 7.64)])
 @pytest.mark.parametrize("with_norm", [False, True])
 @pytest.mark.parametrize("sens_first", [False, True])
 def test_smoothing_matches_oracle(small, sigma, with_norm, sens_first):
@@ -91,6 +97,59 @@ def test_smoothing_matches_oracle(small, sigma, with_norm, sens_first):
                           smooth_before_sensitivity=not sens_first)
     assert np.all(np.isfinite(out))
     np.testing.assert_allclose(out, exp, rtol=SMOOTH_RTOL, atol=1e-300)
+
+
+@pytest.mark.parametrize("with_norm", [False, True])
+def test_smoothed_epilogue_is_an_exact_fp64_product(small, with_norm):
+    """The smoothed path's last step is FP64: with zero-width kernels the
+    FP32 passes carry y = fl32(fl32(acc) fl32(c)) [fl32(norm)] unchanged, and
+    the epilogue multiplies y, widened exactly, by the FP64 reciprocal of the
+    normalisation (0 where it is 0) and then by the FP64 sensitivity, each
+    product rounded to nearest in FP64.  numpy's IEEE arithmetic in the same
+    order gives the result bit for bit."""
+    kw = dict(sens=small.ids["sens_lor"], sigma=(0.0, 0.0, 0.0), scale=2.5)
+    if with_norm:
+        kw["norm"] = small.ids["norm_lor"]
+    out = small.run(**kw).cpu().numpy()
+    y = small.acc.astype(np.float32) * np.float32(math.ldexp(2.5, -32))
+    if with_norm:
+        y = y * small.norm_lor.astype(np.float32)[..., None]
+    x = y.astype(np.float64)
+    if with_norm:
+        nz = small.norm_lor != 0
+        rnorm = np.where(nz, 1.0 / np.where(nz, small.norm_lor, 1.0), 0.0)
+        x = x * rnorm[..., None]
+    exp = x * small.sens_lor[..., None]
+    np.testing.assert_array_equal(out, exp)
+    # against the FP64 oracle, within the FP32 rounding of y
+    ref = oracle.finalize(small.acc, small.sc.n_rings, sens=small.sens_lor,
+                          norm=small.norm_lor if with_norm else None, sigma=(0.0, 0.0, 0.0), scale=2.5)
+    # five FP32 roundings (acc, c, the product, norm, its product), each <= 2^-24 relative
+    np.testing.assert_allclose(out, ref, rtol=6 * 2.0**-24, atol=1e-300)
+
+
+@pytest.mark.parametrize("sigma", [None, (2.0, 2.0, 2.0), (4.25, 2.12, 7.64)])
+@pytest.mark.parametrize("same_stream", [False, True])
+def test_finalize_to_host_equals_device_finalize(small, sigma, same_stream):
+    """psc_finalize_host computes the estimate in parts (plane ranges, or
+    groups of ring-difference segments with smoothing) and copies each part
+    to host memory as it finishes: the host copy equals psc_finalize's device
+    result bit for bit, whether the copies run on their own stream or on the
+    compute stream."""
+    torch = small.torch
+    kw = dict(sens=small.ids["sens_lor"], norm=small.ids["norm_lor"] if sigma else 0, sigma=sigma, scale=0.5)
+    ref = small.run(**kw)
+    host = psc.host_tensor(small.sc.shape, torch.float64)
+    host.fill_(float("nan"))
+    work = torch.full(small.sc.shape, np.nan, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    copy = stream if same_stream else torch.cuda.Stream()
+    psc.psc_finalize_host(small.ctx, psc.finalize_args(small.a_id, **kw), work, host, stream.cuda_stream,
+                          copy.cuda_stream)
+    copy.synchronize()
+    np.testing.assert_array_equal(host.numpy(), ref.cpu().numpy())
+    torch.cuda.synchronize()
+    assert torch.equal(work, ref)
 
 
 def test_smoothing_conserves_mass_and_delta(small):

@@ -25,6 +25,7 @@ def test_host_tensor_is_pinned_and_round_trips(cuda):
     assert h.is_pinned() and h.shape == (3, 1000, 777)
     d = torch.randn(h.shape, dtype=torch.float64, device="cuda")
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())   # d is written on the current stream
     with torch.cuda.stream(s):
         h.copy_(d, non_blocking=True)
     s.synchronize()
