@@ -111,7 +111,15 @@ class Stats(C.Structure):
 class FinalizeArgs(C.Structure):
     _fields_ = [("acc", C.c_int32), ("sens", C.c_int32), ("norm", C.c_int32),
                 ("smooth", C.c_int32), ("sigma", C.c_double * 3), ("scale", C.c_double),
-                ("sens_first", C.c_int32)]
+                ("sens_first", C.c_int32), ("seg_lo", C.c_int32), ("seg_hi", C.c_int32)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("block", C.c_int32), ("grid", C.c_int32), ("chunks_per_cta", C.c_int32),
+                ("max_chunk", C.c_int32), ("rate", C.c_double), ("probed", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Request(C.Structure):
@@ -155,12 +163,15 @@ SIGNATURES = {
     "psc_load_lut": (C.c_int, [_P, C.POINTER(LutDesc), C.POINTER(_I32)]),
     "psc_load_sinogram": (C.c_int, [_P, _I32, _P, _I32, C.POINTER(_I32)]),
     "psc_acc_create": (C.c_int, [_P, _I32, C.POINTER(_I32)]),
+    "psc_acc_wrap": (C.c_int, [_P, _I32, _P, C.POINTER(_I32)]),
     "psc_acc_zero": (C.c_int, [_P, _I32, _P]),
     "psc_acc_read": (C.c_int, [_P, _I32, _P, _P]),
     "psc_acc_write": (C.c_int, [_P, _I32, _P, _P]),
     "psc_simulate": (C.c_int, [_P, C.POINTER(SimArgs), C.POINTER(Stats), _P]),
     "psc_simulate_batch": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Stats), _P]),
     "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
+    "psc_simulate_batch_tuned": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Schedule), _P]),
+    "psc_finalize_host": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P, _P, _P]),
     "psc_finalize_static": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _I32, _P,
                                       C.c_double, _I32, _P, _P]),
     "psc_norm_sinogram": (C.c_int, [_P, _I32, _P, _P, _P]),
@@ -340,6 +351,14 @@ def psc_acc_create(ctx, scanner):
     return i.value
 
 
+def psc_acc_wrap(ctx, scanner, device_tensor):
+    """An accumulator over a caller-owned int64 device tensor (kept alive by
+    the caller until psc_unload)."""
+    i = C.c_int32()
+    _check(lib().psc_acc_wrap(ctx, scanner, _ptr(device_tensor), C.byref(i)))
+    return i.value
+
+
 def psc_acc_zero(ctx, acc, stream=None):
     _check(lib().psc_acc_zero(ctx, acc, _stream(stream)))
 
@@ -367,8 +386,25 @@ def psc_simulate_batch(ctx, args_list, stats=False, stream=None):
     return st.as_dict() if st is not None else None
 
 
+def psc_simulate_batch_tuned(ctx, args_list, stream=None):
+    """psc_simulate_batch with an autotuned launch schedule; returns the
+    schedule (dict: block, grid, chunks_per_cta, max_chunk, rate, probed)."""
+    arr = (SimArgs * len(args_list))(*args_list)
+    sch = Schedule()
+    _check(lib().psc_simulate_batch_tuned(ctx, arr, len(args_list), C.byref(sch), _stream(stream)))
+    return sch.as_dict()
+
+
 def psc_finalize(ctx, args: FinalizeArgs, out, stream=None):
     _check(lib().psc_finalize(ctx, C.byref(args), _ptr(out), _stream(stream)))
+
+
+def psc_finalize_host(ctx, args: FinalizeArgs, work, out_host, stream=None, copy_stream=None):
+    """psc_finalize into the device buffer ``work``, each finished part copied
+    to ``out_host`` (a host tensor, best from host_tensor) on
+    ``copy_stream`` (default: ``stream``)."""
+    _check(lib().psc_finalize_host(ctx, C.byref(args), _ptr(work), _ptr(out_host), _stream(stream),
+                                   _stream(copy_stream if copy_stream is not None else stream)))
 
 
 def psc_finalize_static(acc, n_rings, n_crystals, n_rad, n_tof, out, sens=None, sens_per_lor=True,
@@ -513,7 +549,10 @@ def sim_args(seed, first, n, scanner, phantom, acc, lut=0, bin_mask=PSC_BIN_SCAT
                    int(lm_capacity))
 
 
-def finalize_args(acc, sens=0, norm=0, sigma=None, scale=1.0, sens_first=False):
+def finalize_args(acc, sens=0, norm=0, sigma=None, scale=1.0, sens_first=False, segments=None):
+    """psc_finalize_args; ``segments`` = (lo, hi) finalizes only the planes of
+    ring-difference segments [lo, hi) (default: every plane)."""
     s = (C.c_double * 3)(*(sigma if sigma is not None else (0.0, 0.0, 0.0)))
+    lo, hi = segments if segments is not None else (0, 0)
     return FinalizeArgs(acc, sens, norm, 1 if sigma is not None else 0, s, scale,
-                        1 if sens_first else 0)
+                        1 if sens_first else 0, lo, hi)

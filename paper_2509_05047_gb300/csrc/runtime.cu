@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -18,6 +19,8 @@
 #include <string>
 #include <unordered_map>
 #include <vector>
+#include <map>
+#include <algorithm>
 
 #include <sys/mman.h>
 #include <unistd.h>
@@ -66,8 +69,9 @@ enum Kind { kScannerObj = 1, kMaterialsObj, kPhantomObj, kLutObj, kSinoObj, kAcc
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool own = true;  // false: caller-owned memory (psc_acc_wrap), not freed
   ~DevBuf() {
-    if (p) cudaFree(p);
+    if (p && own) cudaFree(p);
   }
 };
 
@@ -117,7 +121,7 @@ struct SinoObj : Object {
   int32_t scanner = 0;
   int per_lor = 0;
   long long n = 0;
-  DevBuf data, data32, recip32;  // FP64 values, FP32 copy, FP32 reciprocal (made on first use)
+  DevBuf data, data32, recip;  // FP64 values, FP32 copy, FP64 reciprocal (made on first use)
   SinoObj() : Object(kSinoObj) {}
 };
 
@@ -143,6 +147,16 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+namespace psc {
+// launch schedule of a batched transport launch: CTA size and count (0:
+// as many as fit), work items per CTA and request, and the largest work item
+struct Sched {
+  int block = 0, grid = 0;
+  int chunks_per_cta = 2;
+  unsigned long long max_chunk = 65536;
+};
+}  // namespace psc
 
 struct psc_ctx {
   int device = 0;
@@ -172,6 +186,9 @@ struct psc_ctx {
   DevBuf cold;
   cudaEvent_t cold_done = nullptr;
   cudaStream_t upload = nullptr;  // non-blocking stream of alias-table uploads
+  // the batched-launch autotuner's choices, per request mix (scanner,
+  // phantom, LUT of each request, sorted): the schedule and its probed rate
+  std::map<std::vector<std::tuple<int, int, int>>, std::pair<psc::Sched, double>> tuned;
 };
 
 namespace {
@@ -780,6 +797,28 @@ int psc_acc_create(psc_ctx* ctx, int32_t scanner, int32_t* id) {
   return PSC_OK;
 }
 
+int psc_acc_wrap(psc_ctx* ctx, int32_t scanner, int64_t* device, int32_t* id) {
+  if (!ctx || !id || !device) return fail(PSC_EINVAL, "NULL argument");
+  if ((uintptr_t)device % 8) return fail(PSC_EINVAL, "accumulator memory must be 8-byte aligned");
+  GET(ScannerObj, sc, scanner, kScannerObj);
+  DeviceGuard g(ctx->device);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, device) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+      at.device != ctx->device) {
+    cudaGetLastError();
+    return fail(PSC_EINVAL, "accumulator memory is not device memory of the context's device");
+  }
+  auto o = std::make_shared<AccObj>();
+  o->scanner = scanner;
+  o->n = sc->n_bins;
+  o->data.p = device;
+  o->data.bytes = sizeof(long long) * (size_t)o->n;
+  o->data.own = false;
+  o->bytes = 0;
+  *id = add_object(ctx, o);
+  return PSC_OK;
+}
+
 int psc_acc_zero(psc_ctx* ctx, int32_t acc, psc_stream stream) {
   if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
   GET(AccObj, a, acc, kAccObj);
@@ -895,8 +934,10 @@ static int make_job(psc_ctx* ctx, const psc_sim_args* a, Job& jb, int& lut_dtype
   return PSC_OK;
 }
 
-int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
-                       psc_stream stream) {
+using psc::Sched;
+
+static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats, psc_stream stream,
+                      const Sched& sc_in) {
   if (!ctx || (!args && n > 0) || n < 0) return fail(PSC_EINVAL, "NULL argument or negative count");
   std::vector<Job> jobs;
   std::vector<ListmodeOut> lms;
@@ -919,7 +960,7 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
   if (jobs.empty()) return PSC_OK;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int block = n > 0 && args[0].block ? args[0].block : 512;
+  const int block = sc_in.block ? sc_in.block : (n > 0 && args[0].block ? args[0].block : 512);
   std::unique_lock<std::mutex> lk(ctx->stats_mu, std::defer_lock);
   unsigned long long* dstats = nullptr;
   if (stats) {
@@ -948,18 +989,20 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
       ++bp.n_jobs;
     }
     if ((int)smem > ctx->max_smem_optin) return fail(PSC_EINVAL, "material tables need %zu bytes of shared memory", smem);
-    int grid = n > 0 ? args[0].grid : 0;
+    int grid = sc_in.grid ? sc_in.grid : (n > 0 ? args[0].grid : 0);
     if (grid == 0) {
       int per_sm = 0;
       CK(transport_occupancy(dt, block, smem, &per_sm), "occupancy");
       grid = ctx->sms * std::max(per_sm, 1);
     }
-    // work items: chunks sized so every CTA gets a few of each job, within
-    // [1024, 65536] histories
+    // work items: chunks sized so every CTA gets chunks_per_cta of each job,
+    // within [1024, max_chunk] histories
     for (int j = 0; j < bp.n_jobs; ++j) {
       Job& jb = bp.jobs[j];
-      const unsigned long long per = (jb.n + 2ull * grid - 1) / (2ull * grid);
-      jb.chunk = std::min<unsigned long long>(65536, std::max<unsigned long long>(1024, per));
+      const unsigned long long parts = (unsigned long long)sc_in.chunks_per_cta * (unsigned long long)grid;
+      const unsigned long long per = (jb.n + parts - 1) / parts;
+      jb.chunk = std::min<unsigned long long>(std::max<unsigned long long>(1024, sc_in.max_chunk),
+                                              std::max<unsigned long long>(1024, per));
       total += (jb.n + jb.chunk - 1) / jb.chunk;
       bp.chunk_end[j] = total;
     }
@@ -1018,12 +1061,136 @@ int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_st
   return PSC_OK;
 }
 
+int psc_simulate_batch(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_stats* stats,
+                       psc_stream stream) {
+  return batch_impl(ctx, args, n, stats, stream, Sched{});
+}
+
+// The autotuner of batched launches.  Candidate schedules run on
+// consecutive slices of every request's own histories (each slice a fixed
+// fraction of each request's budget, so every probe sees the request mix),
+// timed with events; the fastest runs the rest.  Every history is simulated
+// exactly once into its request's accumulator, and the accumulators do not
+// depend on the schedule (counter-based streams, integer sums), so the
+// result equals psc_simulate_batch's bit for bit.  The choice is cached per
+// request mix (the requests' scanner, phantom and LUT objects).
+static const Sched kTuneCandidates[] = {
+    {512, 0, 2, 65536}, {512, 0, 8, 65536}, {512, 0, 2, 16384}, {512, 0, 16, 8192},
+    {256, 0, 2, 65536}, {256, 0, 8, 16384}};
+constexpr int kTuneSlices = 48;  // a probe takes 1/48 of every request's histories
+
+int psc_simulate_batch_tuned(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_schedule* chosen,
+                             psc_stream stream) {
+  if (!ctx || (!args && n > 0) || n < 0) return fail(PSC_EINVAL, "NULL argument or negative count");
+  for (int i = 0; i < n; ++i)
+    if (args[i].lm_out || args[i].cls_out || args[i].key_out || args[i].q_out)
+      return fail(PSC_EINVAL, "the tuned batch takes no per-history outputs");
+  std::vector<std::tuple<int, int, int>> key;
+  for (int i = 0; i < n; ++i) key.emplace_back(args[i].scanner, args[i].phantom, args[i].lut);
+  std::sort(key.begin(), key.end());
+  std::vector<psc_sim_args> rest(args, args + n);
+  Sched best;
+  double best_rate = 0.0;
+  int probed = 0;
+  auto cached = ctx->tuned.find(key);
+  if (cached != ctx->tuned.end()) {
+    best = cached->second.first;
+    best_rate = cached->second.second;
+  } else {
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    int rc = PSC_OK;
+    for (const Sched& c : kTuneCandidates) {
+      std::vector<psc_sim_args> slice(rest);
+      unsigned long long hist = 0;
+      for (int i = 0; i < n; ++i) {
+        const unsigned long long take = std::min<unsigned long long>(
+            rest[i].n_histories, std::max<unsigned long long>(1024, args[i].n_histories / kTuneSlices));
+        slice[i].n_histories = take;
+        rest[i].first_history += take;
+        rest[i].n_histories -= take;
+        hist += take;
+      }
+      if (hist == 0) break;
+      if ((rc = cudaEventRecord(e0, s) != cudaSuccess ? fail(PSC_EDEVICE, "event") : PSC_OK)) break;
+      if ((rc = batch_impl(ctx, slice.data(), n, nullptr, stream, c))) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(PSC_EDEVICE, "probe timing");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double rate = ms > 0.0f ? (double)hist / (ms * 1e-3) : 0.0;
+      if (rate > best_rate) {
+        best_rate = rate;
+        best = c;
+      }
+      ++probed;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (probed == (int)(sizeof(kTuneCandidates) / sizeof(kTuneCandidates[0]))) ctx->tuned[key] = {best, best_rate};
+  }
+  if (chosen) {
+    chosen->block = best.block;
+    chosen->grid = best.grid;
+    chosen->chunks_per_cta = best.chunks_per_cta;
+    chosen->max_chunk = (int32_t)best.max_chunk;
+    chosen->rate = best_rate;
+    chosen->probed = probed;
+  }
+  return batch_impl(ctx, rest.data(), n, nullptr, stream, best);
+}
+
 int psc_simulate(psc_ctx* ctx, const psc_sim_args* a, psc_stats* stats, psc_stream stream) {
   if (!ctx || !a) return fail(PSC_EINVAL, "NULL argument");
   return psc_simulate_batch(ctx, a, 1, stats, stream);
 }
 
-static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide) {
+// Copies of finished parts of the estimate to host memory, for
+// psc_finalize_host: after each part is written on stream s, copy stream c
+// waits for it and copies it.  One event per part, released when done.
+struct HostCopy {
+  double* host = nullptr;
+  cudaStream_t c = nullptr;
+};
+
+static int copy_planes_2d(double* host, const double* dev, long long plane_elems, long long first_plane,
+                          long long pitch_planes, long long rows, cudaStream_t c) {
+  const size_t width = sizeof(double) * (size_t)plane_elems;
+  const size_t pitch = width * (size_t)pitch_planes;
+  const size_t off = (size_t)first_plane * (size_t)plane_elems;
+  if (rows == 1) {
+    CK(cudaMemcpyAsync(host + off, dev + off, width, cudaMemcpyDeviceToHost, c), "copy to host");
+  } else if (pitch <= (size_t)INT32_MAX) {
+    CK(cudaMemcpy2DAsync(host + off, pitch, dev + off, pitch, width, (size_t)rows, cudaMemcpyDeviceToHost, c),
+       "copy to host");
+  } else {
+    for (long long r = 0; r < rows; ++r)
+      CK(cudaMemcpyAsync(host + off + (size_t)r * pitch_planes * plane_elems, dev + off + (size_t)r * pitch_planes *
+                         plane_elems, width, cudaMemcpyDeviceToHost, c), "copy to host");
+  }
+  return PSC_OK;
+}
+
+// stream c waits for the work enqueued on s so far
+static int join(cudaStream_t c, cudaStream_t s) {
+  if (c == s) return PSC_OK;
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+  cudaError_t e = cudaEventRecord(ev, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c, ev, 0);
+  cudaEventDestroy(ev);  // released once the wait is satisfied
+  CK(e, "order the copy stream");
+  return PSC_OK;
+}
+
+static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide,
+                         const HostCopy* hc = nullptr) {
   if (!ctx || !a || !out) return fail(PSC_EINVAL, "NULL argument");
   GET(AccObj, acc, a->acc, kAccObj);
   GET(ScannerObj, sc, acc->scanner, kScannerObj);
@@ -1058,12 +1225,75 @@ static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, 
   p.smooth = a->smooth ? 1 : 0;
   p.sens_first = a->sens_first ? 1 : 0;
   p.divide_acc = divide;
+  if (a->seg_lo != a->seg_hi) {
+    if (a->seg_lo < 0 || a->seg_hi > 2 * d.n_rings - 1 || a->seg_lo > a->seg_hi)
+      return fail(PSC_EINVAL, "segment range [%d, %d) outside [0, %d)", (int)a->seg_lo, (int)a->seg_hi,
+                  2 * d.n_rings - 1);
+    p.seg_lo = a->seg_lo;
+    p.seg_hi = a->seg_hi;
+  }
   p.magic_T = p.T == 1 ? 0u : (unsigned)(((1ULL << 32) + p.T - 1) / p.T);
   if ((long long)p.V * p.R * p.T * p.T >= (1LL << 32))
     return fail(PSC_EOVERFLOW, "a sinogram plane is too large");
-  if (!p.smooth) {
-    CK(launch_finalize(p, ctx->sms, s), "finalize");
+  const int nr = d.n_rings;
+  const bool all_planes = p.seg_hi <= p.seg_lo;
+  const int s_lo = all_planes ? 0 : p.seg_lo, s_hi = all_planes ? 2 * nr - 1 : p.seg_hi;
+  const int n_planes = finalize_planes(p);
+  const long long J = (long long)p.V * p.R * p.T;  // bins per plane
+  auto seg_len = [&](int sg) { return nr - std::abs(sg - (nr - 1)); };
+  // parts of the estimate copied as they finish: groups of whole segments of
+  // about equal size (plane ranges when every plane is finalized without
+  // smoothing), about kHostParts of them; a group's planes are the rows
+  // ra (n + 1) + d of the layout
+  constexpr int kHostParts = 8;
+  auto for_groups = [&](auto&& run_group) -> int {
+    int lo = s_lo, idx = 0;
+    long long done = 0;
+    for (int k = 1; k <= kHostParts && lo < s_hi; ++k) {
+      const long long target = (long long)n_planes * k / kHostParts;
+      int hi = lo, n_idx = 0;
+      while (hi < s_hi && (done < target || hi == lo)) {
+        done += seg_len(hi);
+        n_idx += seg_len(hi);
+        ++hi;
+      }
+      if (k == kHostParts)
+        while (hi < s_hi) n_idx += seg_len(hi++);
+      int rc = run_group(lo, hi, idx, idx + n_idx);
+      if (!rc) rc = join(hc->c, (cudaStream_t)stream);
+      for (int sg = lo; sg < hi && !rc; ++sg) {
+        const int dd = sg - (nr - 1), ra0 = std::max(0, -dd);
+        rc = copy_planes_2d(hc->host, out, J, (long long)ra0 * (nr + 1) + dd, nr + 1, seg_len(sg), hc->c);
+      }
+      if (rc) return rc;
+      lo = hi;
+      idx += n_idx;
+    }
     return PSC_OK;
+  };
+  if (!p.smooth) {
+    if (!hc) {
+      CK(launch_finalize(p, ctx->sms, s), "finalize");
+      return PSC_OK;
+    }
+    if (all_planes) {
+      for (int k = 0; k < kHostParts; ++k) {
+        const int lo = (int)((long long)n_planes * k / kHostParts), hi = (int)((long long)n_planes * (k + 1) / kHostParts);
+        if (hi <= lo) continue;
+        CK(launch_finalize_planes(p, lo, hi, ctx->sms, s), "finalize");
+        int rc;
+        if ((rc = join(hc->c, s))) return rc;
+        // planes [lo, hi) are contiguous: one copy of (hi - lo) J elements at plane lo
+        CK(cudaMemcpyAsync(hc->host + (size_t)lo * (size_t)J, out + (size_t)lo * (size_t)J,
+                           sizeof(double) * (size_t)J * (size_t)(hi - lo), cudaMemcpyDeviceToHost, hc->c),
+           "copy to host");
+      }
+      return PSC_OK;
+    }
+    return for_groups([&](int, int, int i_lo, int i_hi) -> int {
+      CK(launch_finalize_planes(p, i_lo, i_hi, ctx->sms, s), "finalize");
+      return PSC_OK;
+    });
   }
   {
     const int rc = finalize_plan(p, a->sigma);
@@ -1072,14 +1302,14 @@ static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, 
   if (norm) {
     p.norm = (const double*)norm->data.p;
     p.norm_per_lor = norm->per_lor;
-    if (!norm->recip32.p) {
+    if (!norm->recip.p) {
       int rc;
-      if ((rc = dev_alloc(ctx, norm->recip32, sizeof(float) * norm->n))) return rc;
-      norm->bytes += norm->recip32.bytes;
-      CK(launch_reciprocal((const double*)norm->data.p, nullptr, (float*)norm->recip32.p, norm->n, ctx->sms, s),
+      if ((rc = dev_alloc(ctx, norm->recip, sizeof(double) * norm->n))) return rc;
+      norm->bytes += norm->recip.bytes;
+      CK(launch_reciprocal((const double*)norm->data.p, (double*)norm->recip.p, nullptr, norm->n, ctx->sms, s),
          "reciprocal");
     }
-    p.rnorm32 = (const float*)norm->recip32.p;
+    p.rnorm = (const double*)norm->recip.p;
     p.norm32 = (const float*)norm->data32.p;
   }
   {
@@ -1103,7 +1333,17 @@ static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, 
     }
     p.scratch = (float*)ctx->scratch.p;
     CK(cudaStreamWaitEvent(s, ctx->scratch_done, 0), "order scratch users");
-    CK(launch_finalize(p, ctx->sms, s), "finalize");
+    if (!hc) {
+      CK(launch_finalize(p, ctx->sms, s), "finalize");
+    } else {
+      // the axial pass in groups of whole segments, each copied when written
+      CK(launch_smooth_front(p, s), "finalize");
+      const int rc = for_groups([&](int lo, int hi, int, int) -> int {
+        CK(launch_smooth_axial(p, lo, hi, s), "finalize");
+        return PSC_OK;
+      });
+      if (rc) return rc;
+    }
     CK(cudaEventRecord(ctx->scratch_done, s), "order scratch users");
   }
   return PSC_OK;
@@ -1111,6 +1351,15 @@ static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, 
 
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream) {
   return finalize_impl(ctx, a, out, stream, 0);
+}
+
+int psc_finalize_host(psc_ctx* ctx, const psc_finalize_args* a, double* work, double* out_host, psc_stream stream,
+                      psc_stream copy_stream) {
+  if (!out_host) return fail(PSC_EINVAL, "out_host is NULL");
+  HostCopy hc;
+  hc.host = out_host;
+  hc.c = (cudaStream_t)copy_stream;
+  return finalize_impl(ctx, a, work, stream, 0, &hc);
 }
 
 int psc_norm_sinogram(psc_ctx* ctx, int32_t acc, const double* sigma, double* out, psc_stream stream) {

@@ -91,3 +91,46 @@ def test_batch_of_many_jobs_equals_one_range(ctx):
     psc.psc_simulate_batch(ctx, batch, stream=stream)
     psc.psc_simulate(ctx, psc.sim_args(21, 0, 400_000, s, p, a2), stream=stream)
     np.testing.assert_array_equal(_acc(ctx, a1, sc.n_bins), _acc(ctx, a2, sc.n_bins))
+
+
+def test_tuned_batch_equals_untuned_batch(ctx):
+    """The autotuned batched launch (probes of candidate schedules on slices
+    of every request's own histories, then the fastest on the rest) gives
+    every request exactly the accumulator of the default schedule; a second
+    call on the same request mix takes the cached choice without probes."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    mats = psc.psc_load_materials(ctx, psc.materials_desc(W.standard_materials()).desc)
+    tiny = W.scanner_tiny()
+    s1 = psc.psc_load_scanner(ctx, psc.scanner_desc(tiny))
+    l1 = psc.psc_load_lut(ctx, psc.lut_desc(W.lut_tiny(tiny)).desc)
+    phs = [psc.psc_load_phantom(ctx, psc.phantom_desc(W.phantom_water_cylinder()).desc, mats),
+           psc.psc_load_phantom(ctx, psc.phantom_desc(
+               W.phantom_random_torso(5, (48, 48, 20), voxel=(4.0, 4.0, 4.0))).desc, mats),
+           psc.psc_load_phantom(ctx, psc.phantom_desc(
+               W.phantom_random_torso(6, (64, 64, 24), voxel=(3.5, 3.5, 3.5))).desc, mats)]
+    budgets = [3_000_001, 250_000, 1_700_000]
+    acc_u = [psc.psc_acc_create(ctx, s1) for _ in phs]
+    acc_t = [psc.psc_acc_create(ctx, s1) for _ in phs]
+
+    def args(accs, seed0):
+        return [psc.sim_args(seed0 + i, 13 * i, n, s1, p, a, lut=l1)
+                for i, (p, a, n) in enumerate(zip(phs, accs, budgets))]
+
+    psc.psc_simulate_batch(ctx, args(acc_u, 40), stream=stream)
+    first = psc.psc_simulate_batch_tuned(ctx, args(acc_t, 40), stream=stream)
+    assert first["probed"] >= 4 and first["rate"] > 0 and first["block"] in (256, 512)
+    for a, b in zip(acc_u, acc_t):
+        u = _acc(ctx, a, tiny.n_bins)
+        assert u.sum() > 0
+        np.testing.assert_array_equal(_acc(ctx, b, tiny.n_bins), u)
+    for a in acc_t:
+        psc.psc_acc_zero(ctx, a, stream)
+    again = psc.psc_simulate_batch_tuned(ctx, args(acc_t, 40), stream=stream)
+    assert again["probed"] == 0 and again["block"] == first["block"]
+    for a, b in zip(acc_u, acc_t):
+        np.testing.assert_array_equal(_acc(ctx, b, tiny.n_bins), _acc(ctx, a, tiny.n_bins))
+    with pytest.raises(psc.PscError):
+        key = torch.empty(10, dtype=torch.int64, device="cuda")
+        psc.psc_simulate_batch_tuned(ctx, [psc.sim_args(1, 0, 10, s1, phs[0], acc_t[0], key_out=key)],
+                                     stream=stream)
