@@ -335,6 +335,21 @@ int psc_norm_sinogram(psc_ctx* ctx, int32_t acc, const double* sigma, double* ou
  * Exact integer sums. */
 int psc_acc_mash(psc_ctx* ctx, int32_t acc, int32_t view_factor, int32_t tof_factor,
                  int64_t* out /* device */, psc_stream stream);
+/* Span (segment) mashing (Sec. 4 lists mashing among the ways to need fewer
+ * counts and less smoothing; the paper gives no details, and the usual
+ * Michelogram span is the reading): ring differences d = rb - ra are
+ * grouped into segments of span (odd) consecutive values, segment k
+ * (k = -K..K) holding [k span - (span-1)/2, k span + (span-1)/2] within the
+ * ring range, and the planes of a segment with the same axial sum
+ * z = ra + rb are added.  A segment's output planes run over z from its
+ * smallest |d| to 2 n_rings - 2 minus it (every other z when it holds a
+ * single ring difference); segments follow in order k = -K..K.  out: device
+ * int64 [out_planes][n_crystals / 2][n_rad][n_tof], or NULL to query the
+ * count; *out_planes (may be NULL) receives the number of output planes
+ * (2025 -> 1379 for 45 rings at span 3; span 1 reorders the planes).  Exact
+ * integer sums, each input plane read once.  PSC_EINVAL for an even span. */
+int psc_acc_span(psc_ctx* ctx, int32_t acc, int32_t span, int64_t* out /* device */, int64_t* out_planes,
+                 psc_stream stream);
 /* Sum over the scanner's rotational symmetries (Sec. 2.2.4 averages the
  * sensitivity sinograms over 14 of them): out_acc = sum over the
  * n_crystals / step rotations by k * step crystals (step = crystals per

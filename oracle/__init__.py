@@ -22,7 +22,7 @@ import subprocess
 import numpy as np
 
 from .sinogram import (finalize, finalize_at, gaussian_weights, reflect_index,  # noqa: F401
-                       segment_planes, smooth)
+                       segment_planes, smooth, span_mash, span_segments)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "psc_oracle.c")

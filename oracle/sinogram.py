@@ -188,6 +188,49 @@ def mash(s, view_factor=1, tof_factor=1):
     return s.reshape(p, v // view_factor, view_factor, r, t // tof_factor, tof_factor).sum(axis=(2, 5))
 
 
+def span_segments(n_rings, span):
+    """Segments of span mashing (Sec. 4 names mashing without details; the
+    usual Michelogram span is the reading): ring differences d = rb - ra in
+    groups of `span` (odd) consecutive values, segment k holding
+    [k span - (span-1)/2, k span + (span-1)/2], k = -K..K.  Returns
+    [(k, d_lo, d_hi, zs)]: d clipped to the ring range, and zs the axial sums
+    z = ra + rb that some plane of the segment has (from the segment's
+    smallest |d| to 2 n - 2 minus it; every other one when the segment holds
+    a single ring difference)."""
+    if span < 1 or span % 2 == 0:
+        raise ValueError("span must be odd and >= 1")
+    h = (span - 1) // 2
+    kmax = (n_rings - 1 + h) // span
+    out = []
+    for k in range(-kmax, kmax + 1):
+        d_lo, d_hi = max(k * span - h, -(n_rings - 1)), min(k * span + h, n_rings - 1)
+        m = 0 if d_lo <= 0 <= d_hi else min(abs(d_lo), abs(d_hi))
+        step = 1 if d_hi > d_lo else 2
+        out.append((k, d_lo, d_hi, list(range(m, 2 * n_rings - 1 - m, step))))
+    return out
+
+
+def span_mash(s, n_rings, span):
+    """Span mashing of a sinogram [plane][view][rad][tof] (plane = ra n + rb):
+    output plane (k, z) is the sum of every input plane (ra, rb) whose ring
+    difference lies in segment k and whose ra + rb = z; segments in order
+    k = -K..K, each segment's planes by z ascending.  Brute force over the
+    input planes; integer input gives exact sums."""
+    index, total = {}, 0
+    for k, _, _, zs in span_segments(n_rings, span):
+        for z in zs:
+            index[(k, z)] = total
+            total += 1
+    out = np.zeros((total,) + s.shape[1:], dtype=s.dtype)
+    h = (span - 1) // 2
+    for ra in range(n_rings):
+        for rb in range(n_rings):
+            d = rb - ra
+            k = (abs(d) + h) // span * (1 if d >= 0 else -1)
+            out[index[(k, ra + rb)]] += s[ra * n_rings + rb]
+    return out
+
+
 def _view_rad(n, a, b, rad_off):
     """View and kept-radial index of the LOR between crystals a < b (the
     integer LOR formula of the binning)."""

@@ -19,7 +19,8 @@ import numpy as np
 from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpsc.so")
+# PSC_LIBRARY=debug loads the bounds-checked debug build (libpsc_debug.so)
+LIB_PATH = os.path.join(_HERE, "libpsc_debug.so" if os.environ.get("PSC_LIBRARY") == "debug" else "libpsc.so")
 
 PSC_OK, PSC_EINVAL, PSC_ENOMEM, PSC_ENOTFOUND, PSC_ETIMEOUT, PSC_EDEVICE, PSC_EOVERFLOW = (
     0, -1, -2, -3, -4, -5, -6)
@@ -170,6 +171,7 @@ SIGNATURES = {
     "psc_simulate": (C.c_int, [_P, C.POINTER(SimArgs), C.POINTER(Stats), _P]),
     "psc_simulate_batch": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Stats), _P]),
     "psc_finalize": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P]),
+    "psc_acc_span": (C.c_int, [_P, _I32, _I32, _P, C.POINTER(C.c_int64), _P]),
     "psc_simulate_batch_tuned": (C.c_int, [_P, C.POINTER(SimArgs), _I32, C.POINTER(Schedule), _P]),
     "psc_finalize_host": (C.c_int, [_P, C.POINTER(FinalizeArgs), _P, _P, _P, _P]),
     "psc_finalize_static": (C.c_int, [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _I32, _P,
@@ -191,7 +193,8 @@ _lib = None
 
 
 def lib():
-    """The loaded libpsc.so (raises if it has not been built)."""
+    """The loaded libpsc.so, or libpsc_debug.so with PSC_LIBRARY=debug (raises
+    if it has not been built: there is no fallback)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
@@ -421,6 +424,15 @@ def psc_norm_sinogram(ctx, acc, sigma, out, stream=None):
     """Smoothing-normalisation sinogram smooth(acc) / acc into ``out``."""
     sig = (C.c_double * 3)(*sigma)
     _check(lib().psc_norm_sinogram(ctx, acc, sig, _ptr(out), _stream(stream)))
+
+
+def psc_acc_span(ctx, acc, span, out=None, stream=None):
+    """Span-mash an accumulator into ``out`` (int64 device tensor of
+    [planes][views][rad][tof]); returns the number of output planes (out=None
+    only queries it)."""
+    n = C.c_int64()
+    _check(lib().psc_acc_span(ctx, acc, span, _ptr(out), C.byref(n), _stream(stream)))
+    return n.value
 
 
 def psc_acc_mash(ctx, acc, view_factor, tof_factor, out, stream=None):

@@ -237,9 +237,12 @@ __global__ void __launch_bounds__(256) finalize_plain_kernel(const __grid_consta
   const long long base = plane * J;
   const long long lor0 = plane * (long long)P.V * P.R;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < J; j += gridDim.x * blockDim.x) {
-    const long long i = base + j;
+    const long long i = dbg_idx(P.dbg, kSiteFinBin, base + j, P.n_bins);
     double x = dmul(i64_to_f64(__ldg(P.acc + i)), P.c);
-    if (P.sens) x = dmul(x, at(P.sens, P.sens_per_lor ? lor0 + fdiv((unsigned)j, P.magic_T) : i));
+    if (P.sens)
+      x = dmul(x, at(P.sens, P.sens_per_lor ? dbg_idx(P.dbg, kSiteFinLor, lor0 + fdiv((unsigned)j, P.magic_T),
+                                                      P.n_bins / P.T)
+                                            : i));
     P.out[i] = x;
   }
 }
@@ -338,6 +341,12 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_radial_kernel(const __g
   const long long line = plane_at(P, blockIdx.y) * P.V + v;
   const int R = P.R, T = P.T;
   const long long base = line * R * T + t;  // bin of (line, r = 0, t)
+#if PSC_DEBUG
+  // the column's rows 0 .. R - 1 (reflection stays inside them) and its LORs
+  if (dbg_idx(P.dbg, kSiteFinColumn, base + (long long)(R - 1) * T, P.n_bins) != base + (long long)(R - 1) * T ||
+      dbg_idx(P.dbg, kSiteFinLor, line * R + R - 1, P.n_bins / T) != line * R + R - 1)
+    return;
+#endif
   const float cf = (float)P.c;
   const bool per_bin_factor = (P.sens_first && P.sens) || P.norm;
   float* dst = reinterpret_cast<float*>(P.out) + base;
@@ -369,6 +378,10 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
   const long long base = plane_at(P, blockIdx.y) * P.V * I + i;
+#if PSC_DEBUG
+  if (dbg_idx(P.dbg, kSiteFinColumn, base + (long long)(P.V - 1) * I, P.n_bins) != base + (long long)(P.V - 1) * I)
+    return;
+#endif
   const float* src = reinterpret_cast<const float*>(P.out) + base;
   float* dst = P.scratch + base;
   auto cvt = [](float x, int) { return x; };
@@ -409,6 +422,12 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
   const long long lors = (long long)P.V * P.R;
   const long long lor0 = p0 * lors + (long long)v * P.R + fdiv((unsigned)i, P.magic_T);
   const long long lor_step = (long long)(nr + 1) * lors;
+#if PSC_DEBUG
+  // the column's planes 0 .. L - 1 and their LORs
+  if (dbg_idx(P.dbg, kSiteFinColumn, bin0 + (L - 1) * bin_step, P.n_bins) != bin0 + (L - 1) * bin_step ||
+      dbg_idx(P.dbg, kSiteFinLor, lor0 + (L - 1) * lor_step, P.n_bins / P.T) != lor0 + (L - 1) * lor_step)
+    return;
+#endif
   auto cvt = [](float x, int) { return x; };
   const bool use_sens = !P.sens_first && P.sens;
   // the epilogue in FP64: the smoothed FP32 value widened exactly, times the

@@ -8,6 +8,8 @@
 // with the integer LOR formula of the binning: for crystals a < b, f = a + b
 // (f -= n and s = -1 when f >= n, else s = +1), view = f >> 1, radial
 // s (n/2 - (b - a)) + n/2 - 1 less the centred clip offset.
+#include <algorithm>
+
 #include "psc_internal.h"
 
 namespace psc {
@@ -154,7 +156,68 @@ __global__ void rotate_orbit_kernel(const long long* __restrict__ in, long long*
   }
 }
 
+// Span mashing: the segment of span-mashed output plane o, and its axial sum
+// z = ra + rb.  Segment k (k = -K..K) holds the ring differences
+// [k span - h, k span + h] (h = (span - 1) / 2) within the ring range, and
+// the axial sums from its smallest |d| to 2 n - 2 minus it (every other one
+// when it holds a single ring difference); output planes run over the
+// segments in order, each by z ascending.
+struct SpanPlane {
+  int d_lo, d_hi, z;
+};
+
+__host__ __device__ inline int span_count(int n, int span, int k, int& d_lo, int& d_hi, int& m, int& step) {
+  const int h = (span - 1) / 2;
+  d_lo = max(k * span - h, -(n - 1));
+  d_hi = min(k * span + h, n - 1);
+  m = (d_lo <= 0 && 0 <= d_hi) ? 0 : min(abs(d_lo), abs(d_hi));
+  step = d_hi > d_lo ? 1 : 2;
+  return (2 * n - 2 - 2 * m) / step + 1;
+}
+
+__device__ inline SpanPlane span_plane(int n, int span, int o) {
+  const int K = (n - 1 + (span - 1) / 2) / span;
+  int d_lo = 0, d_hi = 0, m = 0, step = 1;
+  for (int k = -K; k <= K; ++k) {
+    const int c = span_count(n, span, k, d_lo, d_hi, m, step);
+    if (o < c || k == K) break;
+    o -= c;
+  }
+  return SpanPlane{d_lo, d_hi, m + o * step};
+}
+
+// grid (column blocks, output planes): each output bin sums the input planes
+// (ra, rb) of its segment with ra + rb = z, read once each (exact int64)
+__global__ void __launch_bounds__(256) span_kernel(const long long* __restrict__ in, long long* __restrict__ out,
+                                                   int n, int span, long long J) {
+  const SpanPlane sp = span_plane(n, span, (int)blockIdx.y);
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (long long)gridDim.x * blockDim.x) {
+    long long sum = 0;
+    for (int d = sp.d_lo; d <= sp.d_hi; ++d) {
+      if ((sp.z + d) & 1) continue;
+      const int ra = (sp.z - d) / 2, rb = (sp.z + d) / 2;
+      if (ra >= 0 && ra < n && rb >= 0 && rb < n) sum += __ldg(in + (long long)(ra * n + rb) * J + j);
+    }
+    out[(long long)blockIdx.y * J + j] = sum;
+  }
+}
+
 }  // namespace
+
+int span_planes(int n_rings, int span) {
+  const int K = (n_rings - 1 + (span - 1) / 2) / span;
+  int total = 0, d_lo, d_hi, m, step;
+  for (int k = -K; k <= K; ++k) total += span_count(n_rings, span, k, d_lo, d_hi, m, step);
+  return total;
+}
+
+cudaError_t launch_span(const long long* in, long long* out, int n_rings, int span, long long J, int sms,
+                        cudaStream_t s) {
+  const int planes = span_planes(n_rings, span);
+  const long long per = std::max(1LL, std::min((J + 255) / 256, 8LL * sms / planes + 1));
+  span_kernel<<<dim3((unsigned)per, (unsigned)planes), 256, 0, s>>>(in, out, n_rings, span, J);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
                         cudaStream_t s) {

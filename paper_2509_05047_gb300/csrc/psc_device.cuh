@@ -13,7 +13,48 @@
 
 #include "psc.h"
 
+#ifndef PSC_DEBUG
+#define PSC_DEBUG 0
+#endif
+
 namespace psc {
+
+// ---------------------------------------------------------------------------
+// Bounds-checked debug build (PSC_DEBUG=1; libpsc_debug.so).  Every indexed
+// access on the hot path passes its index through dbg_idx: an index outside
+// [0, bound) is recorded (the first one in full, all of them counted) and
+// replaced by 0, so the access stays inside its array, the kernel finishes,
+// and the host call that launched it fails with PSC_EDEVICE naming the site.
+// Release builds compile the checks out.
+// ---------------------------------------------------------------------------
+enum : unsigned {
+  kSiteSelfTest = 0, kSiteAlias = 1, kSiteVoxel = 2, kSiteMaterial = 3, kSiteKappa = 4, kSiteLut = 5,
+  kSiteAcc = 6, kSiteHistOut = 7, kSiteSlot = 8, kSiteFinBin = 9, kSiteFinLor = 10, kSiteFinColumn = 11
+};
+
+struct DebugRecord {
+  unsigned long long count;    // violations seen
+  unsigned long long index, bound;
+  unsigned site, pad;
+};
+
+__device__ __forceinline__ long long dbg_idx(DebugRecord* rec, unsigned site, long long i, long long bound) {
+#if PSC_DEBUG
+  if ((unsigned long long)i >= (unsigned long long)bound) {
+    if (rec && atomicAdd(&rec->count, 1ull) == 0ull) {
+      rec->site = site;
+      rec->index = (unsigned long long)i;
+      rec->bound = (unsigned long long)bound;
+    }
+    return 0;
+  }
+#else
+  (void)rec;
+  (void)site;
+  (void)bound;
+#endif
+  return i;
+}
 
 constexpr int kMaxMaterials = 8;
 constexpr int kMaxSteps = 4096;     // Woodcock steps per photon (safety bound)
@@ -74,6 +115,7 @@ struct LutParams {
   // entries between successive transaxial / axial positions; 0 on a position axis of one
   // bin (a LUT without crystal information), so every photon reads position 0
   long long t_stride, a_stride;
+  long long size;              // entries (bounds checks of the debug build)
 };
 
 // one simulation request: histories [first, first + n) of seed's streams
@@ -109,6 +151,7 @@ struct BatchParams {
   unsigned long long* next_chunk;  // work counter, zero at launch
   unsigned long long* stats;       // kStatCount counters or nullptr
   uint32_t* cold;                  // per-CTA slot fields kept out of shared memory
+  DebugRecord* dbg;                // bounds-check record of the debug build
   ListmodeOut lm[kMaxJobs];
 };
 static_assert(sizeof(BatchParams) <= 32764, "kernel parameter space");
@@ -184,7 +227,7 @@ __device__ __forceinline__ float lut_load(const void* p, int i) {
 
 template <int DT>
 __device__ __forceinline__ float lut_prob(const LutParams& L, float e, float a, float b, int tpos,
-                                          int apos) {
+                                          int apos, DebugRecord* dbg = nullptr) {
   if (DT < 0) return 1.0f;
   int e0, e1, a0, a1, b0, b1;
   float fe, fa, fb;
@@ -192,7 +235,16 @@ __device__ __forceinline__ float lut_prob(const LutParams& L, float e, float a, 
   lut_axis(a, L.a_min, L.a_scale, L.n_a, a0, a1, fa);
   lut_axis(b, L.b_min, L.b_scale, L.n_b, b0, b1, fb);
   // the (tpos, apos) block, then 32-bit offsets inside it
-  const long long pos = (long long)apos * L.a_stride + (long long)tpos * L.t_stride;
+  long long pos = (long long)apos * L.a_stride + (long long)tpos * L.t_stride;
+#if PSC_DEBUG
+  {  // the block's first and last taps, or block 0 at taps 0
+    const long long last = pos + ((long long)(e1 * L.n_a + a1) * L.n_b + b1);
+    if (dbg_idx(dbg, kSiteLut, last, L.size) != last || dbg_idx(dbg, kSiteLut, pos, L.size) != pos) {
+      pos = 0;
+      e0 = e1 = a0 = a1 = b0 = b1 = 0;
+    }
+  }
+#endif
   const void* p = DT == 0 ? (const void*)(reinterpret_cast<const float*>(L.data) + pos)
                           : (const void*)(reinterpret_cast<const __half*>(L.data) + pos);
   const int r00 = (e0 * L.n_a + a0) * L.n_b, r01 = (e0 * L.n_a + a1) * L.n_b;

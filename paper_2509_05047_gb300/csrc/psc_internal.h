@@ -33,6 +33,7 @@ struct FinParams {
   int plane0;                  // first plane (index into the launch's planes) of a plain launch
   int seg0;                    // first ring-difference segment of an axial-pass launch
   int seg_lo, seg_hi;          // finalize only the planes of segments [seg_lo, seg_hi); equal: all
+  DebugRecord* dbg;            // bounds-check record of the debug build (nullptr: none)
   int divide_acc;              // output smoothed / (acc * c), 0 where acc == 0 (normalisation sinogram)
   unsigned magic_T;            // ceil(2^32 / T) for exact i / T, 0 when T == 1
   int K[3];                    // truncation radius per axis (radial, view, axial)
@@ -70,6 +71,10 @@ cudaError_t launch_smooth_front(const FinParams& p, cudaStream_t s);
 cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t s);
 // sinogram post-processing of int64 accumulators (postproc.cu)
 cudaError_t launch_mash(const long long* in, long long* out, int planes, int V, int R, int T, int vf, int tf,
+                        cudaStream_t s);
+// span mashing: output planes of n_rings rings at span (odd), and the launch
+int span_planes(int n_rings, int span);
+cudaError_t launch_span(const long long* in, long long* out, int n_rings, int span, long long J, int sms,
                         cudaStream_t s);
 cudaError_t launch_rotate_sum(const long long* in, long long* out, int n_crystals, int n_rings, int R, int T,
                               int step, cudaStream_t s);

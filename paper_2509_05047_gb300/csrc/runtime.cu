@@ -179,6 +179,7 @@ struct psc_ctx {
   // work counters of the persistent transport launches: a ring of slots,
   // each zeroed on the launch's stream before use
   DevBuf counters;
+  DevBuf dbg;                     // bounds-check record (DebugRecord) of the debug build
   unsigned long long counter_next = 0;
   // slot fields the transport kernel keeps in global memory, grown on
   // demand; launches on different streams are ordered through cold_done
@@ -190,6 +191,30 @@ struct psc_ctx {
   // phantom, LUT of each request, sorted): the schedule and its probed rate
   std::map<std::vector<std::tuple<int, int, int>>, std::pair<psc::Sched, double>> tuned;
 };
+
+// Debug builds: after a call's launches, wait for them and fail with
+// PSC_EDEVICE if a bounds check caught an index (the record is then cleared).
+static int debug_check(psc_ctx* ctx, cudaStream_t s, const char* what) {
+#if PSC_DEBUG
+  static const char* const kSites[] = {"self-test", "alias table", "voxel", "material id", "Rayleigh kappa",
+                                       "LUT tap", "accumulator bin", "per-history output", "slot",
+                                       "finalize bin", "finalize LOR factor", "smoothing column"};
+  psc::DebugRecord r;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&r, ctx->dbg.p, sizeof r, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(PSC_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+  if (r.count) {
+    cudaMemset(ctx->dbg.p, 0, sizeof r);
+    return fail(PSC_EDEVICE, "bounds check failed in %s: %llu accesses out of range, the first at %s (index %llu, bound %llu)",
+                what, r.count, r.site < 12 ? kSites[r.site] : "?", r.index, r.bound);
+  }
+#else
+  (void)ctx;
+  (void)s;
+  (void)what;
+#endif
+  return PSC_OK;
+}
 
 namespace {
 
@@ -348,6 +373,11 @@ int psc::psc_set_error(int code, const char* fmt, ...) {
 
 extern "C" {
 
+#if PSC_DEBUG
+// a known violation per lane (index 5 of 3): the record must count 32 and keep one
+__global__ void debug_selftest_kernel(DebugRecord* r) { (void)dbg_idx(r, kSiteSelfTest, 5, 3); }
+#endif
+
 int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
   if (!out) return fail(PSC_EINVAL, "out is NULL");
   *out = nullptr;
@@ -379,6 +409,25 @@ int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
     return cuda_fail(e, "cudaMalloc(counters)");
   }
   ctx->counters.bytes = sizeof(unsigned long long) * kCounterSlots;
+  e = cudaMalloc(&ctx->dbg.p, sizeof(DebugRecord));
+  if (e == cudaSuccess) e = cudaMemset(ctx->dbg.p, 0, sizeof(DebugRecord));
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaMalloc(debug record)");
+  }
+  ctx->dbg.bytes = sizeof(DebugRecord);
+#if PSC_DEBUG
+  {  // the checks record what they catch: a known violation, then a clean record
+    DebugRecord r;
+    debug_selftest_kernel<<<1, 32>>>((DebugRecord*)ctx->dbg.p);
+    e = cudaMemcpy(&r, ctx->dbg.p, sizeof r, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->dbg.p, 0, sizeof(DebugRecord));
+    if (e != cudaSuccess || r.count != 32 || r.site != kSiteSelfTest || r.index != 5 || r.bound != 3) {
+      delete ctx;
+      return e != cudaSuccess ? cuda_fail(e, "debug self-test") : fail(PSC_EDEVICE, "debug self-test: record not kept");
+    }
+  }
+#endif
   e = cudaEventCreateWithFlags(&ctx->scratch_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->cold_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking);
@@ -426,6 +475,12 @@ size_t huge_page_bytes() {
 
 extern "C" {
 
+#ifdef MADV_COLLAPSE
+constexpr int kMadvCollapse = MADV_COLLAPSE;
+#else
+constexpr int kMadvCollapse = 25;  // Linux's value for MADV_COLLAPSE
+#endif
+
 int psc_host_alloc(uint64_t bytes, void** ptr) {
   if (!ptr) return fail(PSC_EINVAL, "ptr is NULL");
   *ptr = nullptr;
@@ -445,6 +500,9 @@ int psc_host_alloc(uint64_t bytes, void** ptr) {
   const long pg = sysconf(_SC_PAGESIZE);
   const size_t step = pg > 0 ? (size_t)pg : 4096;
   for (size_t i = 0; i < len; i += step) p[i] = 0;  // fault in now, as huge pages where possible
+  // where a fault found no free huge page (fragmented memory), collapse the
+  // range into huge pages now (Linux 6.1+; ignored where unsupported)
+  madvise(p, len, kMadvCollapse);
   const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -759,6 +817,7 @@ int psc_load_lut(psc_ctx* ctx, const psc_lut_desc* d, int32_t* id) {
   const long long block = (long long)d->n_e * d->n_a * d->n_b;
   L.t_stride = d->n_tpos > 1 ? block : 0;
   L.a_stride = d->n_apos > 1 ? block * d->n_tpos : 0;
+  L.size = block * d->n_tpos * d->n_apos;
   *id = add_object(ctx, o);
   return PSC_OK;
 }
@@ -1011,6 +1070,7 @@ static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_sta
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s), "zero work counter");
     bp.next_chunk = counter;
     bp.stats = dstats;
+    bp.dbg = (DebugRecord*)ctx->dbg.p;
     std::lock_guard<std::mutex> cl(ctx->cold_mu);
     const size_t cold_bytes = sizeof(uint32_t) * transport_cold_words(grid, block);
     if (ctx->cold.bytes < cold_bytes) {
@@ -1039,6 +1099,10 @@ static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_sta
       else CK(cudaStreamWaitEvent(s, ph->last_use, 0), "order phantom users");
       CK(cudaEventRecord(ph->last_use, s), "phantom event");
     }
+  }
+  {
+    const int rc = debug_check(ctx, s, "the transport kernel");
+    if (rc) return rc;
   }
   if (stats) {
     unsigned long long h[kStatCount];
@@ -1189,8 +1253,17 @@ static int join(cudaStream_t c, cudaStream_t s) {
   return PSC_OK;
 }
 
+static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide,
+                             const HostCopy* hc);
+
 static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide,
                          const HostCopy* hc = nullptr) {
+  const int rc = finalize_launches(ctx, a, out, stream, divide, hc);
+  return rc ? rc : debug_check(ctx, (cudaStream_t)stream, "finalize");
+}
+
+static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* out, psc_stream stream, int divide,
+                             const HostCopy* hc) {
   if (!ctx || !a || !out) return fail(PSC_EINVAL, "NULL argument");
   GET(AccObj, acc, a->acc, kAccObj);
   GET(ScannerObj, sc, acc->scanner, kScannerObj);
@@ -1225,6 +1298,7 @@ static int finalize_impl(psc_ctx* ctx, const psc_finalize_args* a, double* out, 
   p.smooth = a->smooth ? 1 : 0;
   p.sens_first = a->sens_first ? 1 : 0;
   p.divide_acc = divide;
+  p.dbg = (DebugRecord*)ctx->dbg.p;
   if (a->seg_lo != a->seg_hi) {
     if (a->seg_lo < 0 || a->seg_hi > 2 * d.n_rings - 1 || a->seg_lo > a->seg_hi)
       return fail(PSC_EINVAL, "segment range [%d, %d) outside [0, %d)", (int)a->seg_lo, (int)a->seg_hi,
@@ -1371,6 +1445,22 @@ int psc_norm_sinogram(psc_ctx* ctx, int32_t acc, const double* sigma, double* ou
   for (int i = 0; i < 3; ++i) a.sigma[i] = sigma[i];
   a.scale = 1.0;
   return finalize_impl(ctx, &a, out, stream, 1);
+}
+
+int psc_acc_span(psc_ctx* ctx, int32_t acc, int32_t span, int64_t* out, int64_t* out_planes, psc_stream stream) {
+  if (!ctx) return fail(PSC_EINVAL, "ctx is NULL");
+  GET(AccObj, a, acc, kAccObj);
+  GET(ScannerObj, sc, a->scanner, kScannerObj);
+  const psc_scanner_desc& d = sc->desc;
+  if (span < 1 || !(span & 1)) return fail(PSC_EINVAL, "span %d must be odd and >= 1", (int)span);
+  const int planes = span_planes(d.n_rings, span);
+  if (out_planes) *out_planes = planes;
+  if (!out) return PSC_OK;
+  DeviceGuard g(ctx->device);
+  CK(launch_span((const long long*)a->data.p, (long long*)out, d.n_rings, span,
+                 (long long)(d.n_crystals / 2) * d.n_rad * d.n_tof, ctx->sms, (cudaStream_t)stream),
+     "span mashing");
+  return PSC_OK;
 }
 
 int psc_acc_mash(psc_ctx* ctx, int32_t acc, int32_t view_factor, int32_t tof_factor, int64_t* out,

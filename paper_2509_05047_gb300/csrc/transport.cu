@@ -228,9 +228,7 @@ __device__ __forceinline__ void angles(float nx, float ny, float3 d, float& alph
 // kDebug: statistics counters and per-history listmode outputs are compiled
 // in only when a launch asks for them, so the production loop stays small.
 // kOneJob (production launches of a single job with an f32 LUT, the common
-// case): the sections read the job's parameters straight from the kernel
-// parameter space, where they are instruction operands, instead of from the
-// shared-memory copy that multi-job launches stage per chunk.
+// case): the job's index in the kernel parameter space is the constant 0.
 // kFixed (production launches of 512-thread CTAs, the default): the slot
 // count is a compile-time constant, so every slot field access is an
 // immediate offset from the slot's address (measured 10 % faster).
@@ -241,7 +239,6 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
   const int n_slots = kFixed ? 16 * kSlotsPerWarp : (int)(bdim >> 5) * kSlotsPerWarp;
   uint32_t* slots = reinterpret_cast<uint32_t*>(smem);  // [kFields][n_slots]
   float4* s_xs = reinterpret_cast<float4*>(slots + kFields * n_slots);
-  __shared__ Job s_job;                       // the job of the current chunk
   __shared__ int s_j;
   __shared__ unsigned long long s_lo;         // first history of the chunk
   __shared__ unsigned s_len, s_next;          // chunk length, next offset to hand out
@@ -283,10 +280,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     const int jcur = s_j;
     if (jcur < 0) break;
     const ListmodeOut lm = kDebug ? B.lm[jcur] : ListmodeOut{nullptr, nullptr, 0};
-    if (jcur != cached) {  // stage the job and its phantom's tables
-      const int* src = reinterpret_cast<const int*>(&B.jobs[jcur]);
-      for (int i = tid; i < (int)(sizeof(Job) / sizeof(int)); i += bdim)
-        reinterpret_cast<int*>(&s_job)[i] = src[i];
+    if (jcur != cached) {  // stage the job's phantom tables
       const PhantomParams& pg = B.jobs[jcur].ph;
       const int n_xs = pg.n_mat * pg.n_tab;
       float* s_maj = reinterpret_cast<float*>(s_xs + n_xs);
@@ -301,9 +295,13 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     }
     __syncthreads();
 
+    // the job's parameters, read from the kernel parameter space (a
+    // compile-time index for single-job launches, the CTA-uniform chunk's job
+    // otherwise): operands of the instructions, not registers held across the
+    // loop (a shared-memory copy made the multi-job instantiations spill)
     const Job& J = [&]() -> const Job& {
       if constexpr (kOneJob) return B.jobs[0];
-      else return s_job;
+      else return B.jobs[jcur];
     }();
     const PhantomParams& ph = J.ph;
     const ScannerParams& S = J.sc;
@@ -336,7 +334,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
     // a history ends in slot g: record its class (and bin, weight), start the next
     auto finish = [&](int g, int cls, long long key_out, long long q_out) {
       const unsigned long long h = (unsigned long long)U(F_HHI, g) << 32 | U(F_HLO, g);
-      const unsigned long long i = h - J.first;
+      const unsigned long long i = (unsigned long long)dbg_idx(B.dbg, kSiteHistOut, (long long)(h - J.first),
+                                                               (long long)J.n);
       if (kDebug) {
         if (J.cls_out) J.cls_out[i] = (int8_t)cls;
         if (J.key_out) J.key_out[i] = key_out;
@@ -391,7 +390,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         if (r < 32) s_sel[warp][r] = g1;
       }
       __syncwarp();
-      const int g = (int)lane_id < min(32, n0 + __popc(sm1)) ? s_sel[warp][lane_id] : -1;
+      const int g = (int)lane_id < min(32, n0 + __popc(sm1))
+                        ? (int)dbg_idx(B.dbg, kSiteSlot, s_sel[warp][lane_id], n_slots) : -1;
       __syncwarp();
 
       if (g >= 0) {
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
         if (sec == kEmit) {
           const uint32_t w0 = word(0), w1 = word(1);
           const unsigned col = __umulhi(w0, (unsigned)ph.n_vox);  // n_vox < 2^31
-          const uint2 at = __ldg(ph.alias + col);
+          const uint2 at = __ldg(ph.alias + dbg_idx(B.dbg, kSiteAlias, col, ph.n_vox));
           const int v = ((w1 >> 9) < at.x) ? (int)col : (int)at.y;
           // v = (iz ny + iy) nx + ix: quotients from a multiply-high with floor(2^32 / d),
           // at most one below the true quotient, then one correction
@@ -500,8 +500,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
                 setF(F_PZ, g, qz);
                 setF(F_PATH, g, Fv(F_PATH, g) + dist);
                 U(F_CNT, g) = cnt + 1u;
-                const float2 vx = __ldg(ph.vox + (unsigned)((iz * ph.ny + iy) * ph.nx + ix));  // n_vox < 2^31
-                const int mat = __float_as_int(vx.y);
+                const float2 vx = __ldg(ph.vox + dbg_idx(B.dbg, kSiteVoxel, (unsigned)((iz * ph.ny + iy) * ph.nx + ix),
+                                                         ph.n_vox));  // n_vox < 2^31
+                const int mat = (int)dbg_idx(B.dbg, kSiteMaterial, __float_as_int(vx.y), ph.n_mat);
                 const float4 cum = interp_xs(s_xs + mat * ph.n_tab, ph.n_tab, ph.e0, e);
                 const float t = uni(k) * mu_max;
                 ++k;
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
           const uint32_t tries = U(F_TRIES, g) + 1u;
           const float e = Fv(F_E, g);
           const float er = e / kRestKeV;
-          const float b = s_kappa[tries >> 16] * er * er;
+          const float b = s_kappa[dbg_idx(B.dbg, kSiteKappa, tries >> 16, ph.n_mat)] * er * er;
           const float sv = u1 / (1.0f + b * (1.0f - u1));
           const float c = 1.0f - 2.0f * sv;
           count(true, kStatTries);
@@ -724,8 +725,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
               b_tp = (int)(pb & 0xffffu);
               b_ap = (int)(pb >> 16);
             }
-            const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_tp, a_ap) *
-                            lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_tp, b_ap);
+            const float w = lut_prob<DT>(J.lut, Cv(C_AE, g), aa, ab, a_tp, a_ap, B.dbg) *
+                            lut_prob<DT>(J.lut, Fv(F_E, g), ba, bb, b_tp, b_ap, B.dbg);
             q = __float2ll_rn(w * 4294967296.0f);
           }
           if (kDebug && lm.out) {
@@ -770,7 +771,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const __grid_constant
             const unsigned hi = __reduce_add_sync(peers, (unsigned)(q >> 16));
             const unsigned lo = __reduce_add_sync(peers, (unsigned)(q & 0xffff));
             if (lane_id == (unsigned)(__ffs(peers) - 1)) {
-              atomicAdd(J.acc + key_, ((unsigned long long)hi << 16) + lo);
+              atomicAdd(J.acc + dbg_idx(B.dbg, kSiteAcc, key_,
+                                        (long long)S.n_rings * S.n_rings * S.n_views * S.n_rad * S.n_tof),
+                        ((unsigned long long)hi << 16) + lo);
               if (stats) atomicAdd(&s_cnt[kStatAtomics], 1ull);
             }
             if (stats) {

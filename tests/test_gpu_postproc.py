@@ -106,3 +106,26 @@ def test_normalisation_sinogram_matches_oracle(env):
     exp = S.norm_from_sinogram(x.astype(np.float64), sc.n_rings, sigma)
     assert np.all(got[x == 0] == 0.0)
     np.testing.assert_allclose(got, exp, rtol=SMOOTH_RTOL, atol=1e-300)
+
+
+@pytest.mark.parametrize("n_rings,span", [(9, 1), (9, 3), (9, 5), (9, 7), (9, 17), (11, 3)])
+def test_span_mashing_matches_oracle(env, n_rings, span):
+    """Span (segment) mashing: the output plane count and every exact int64
+    sum equal the oracle's brute force over the input planes."""
+    ctx, torch = env
+    sc = W.scanner_small(n_crystals=38, n_rings=n_rings, n_tof=3, n_rad=33)
+    rng = np.random.default_rng(span * 31 + n_rings)
+    acc = rng.integers(0, 1 << 40, size=sc.shape, dtype=np.int64)
+    s_id, a_id = _acc(ctx, torch, sc, acc)
+    exp = S.span_mash(acc, n_rings, span)
+    planes = psc.psc_acc_span(ctx, a_id, span)
+    assert planes == exp.shape[0]
+    out = torch.full((planes,) + sc.shape[1:], -1, dtype=torch.int64, device="cuda")
+    assert psc.psc_acc_span(ctx, a_id, span, out, torch.cuda.current_stream().cuda_stream) == planes
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), exp)
+    with pytest.raises(psc.PscError) as e:
+        psc.psc_acc_span(ctx, a_id, 2)
+    assert e.value.code == psc.PSC_EINVAL
+    psc.psc_unload(ctx, a_id)
+    psc.psc_unload(ctx, s_id)

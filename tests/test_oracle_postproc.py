@@ -71,3 +71,50 @@ def test_normalisation_sinogram_of_a_constant_is_one_and_scale_free():
     sm = S.smooth(x, sc.n_rings, (2.0, 1.5, 1.0))
     ok = x != 0
     np.testing.assert_allclose(sm[ok] / n1[ok], x[ok], rtol=1e-12)
+
+
+def test_span_mashing_hand_example():
+    """3 rings, span 3: ring differences -1..1 form segment 0 (axial sums
+    z = 0..4), d = +-2 the outer segments (z = 2 only).  With plane p holding
+    the value p (plane = ra 3 + rb): segment -1 is (2, 0) = 6; segment 0 is
+    z=0: (0,0) = 0, z=1: (0,1) + (1,0) = 4, z=2: (1,1) = 4, z=3: (1,2) + (2,1)
+    = 12, z=4: (2,2) = 8; segment +1 is (0, 2) = 2."""
+    assert oracle.span_segments(3, 3) == [(-1, -2, -2, [2]), (0, -1, 1, [0, 1, 2, 3, 4]), (1, 2, 2, [2])]
+    s = np.arange(9, dtype=np.int64).reshape(9, 1, 1, 1)
+    np.testing.assert_array_equal(oracle.span_mash(s, 3, 3).ravel(), [6, 0, 4, 4, 12, 8, 2])
+
+
+@pytest.mark.parametrize("n_rings,span", [(9, 1), (9, 3), (9, 5), (9, 7), (9, 17), (45, 3), (45, 11)])
+def test_span_mashing_conserves_counts_and_plane_count(n_rings, span):
+    rng = np.random.default_rng(n_rings * 100 + span)
+    s = rng.integers(0, 1 << 30, size=(n_rings * n_rings, 2, 3, 2), dtype=np.int64)
+    out = oracle.span_mash(s, n_rings, span)
+    np.testing.assert_array_equal(out.sum(axis=0), s.sum(axis=0))
+    segs = oracle.span_segments(n_rings, span)
+    assert out.shape[0] == sum(len(zs) for *_, zs in segs)
+    # every ring difference falls in exactly one segment, and every output
+    # plane receives at least one input plane
+    ds = [d for _, lo, hi, _ in segs for d in range(lo, hi + 1)]
+    ones = oracle.span_mash(np.ones((n_rings * n_rings, 1, 1, 1), np.int64), n_rings, span).ravel()
+    assert ones.min() >= 1 and ones.sum() == n_rings * n_rings
+    assert sorted(ds) == list(range(-(n_rings - 1), n_rings))
+
+
+def test_span_one_is_a_plane_permutation():
+    n = 7
+    s = (np.arange(n * n, dtype=np.int64) * 1000 + 7).reshape(n * n, 1, 1, 1)
+    out = oracle.span_mash(s, n, 1).ravel()
+    assert out.size == n * n and sorted(out) == sorted(s.ravel())
+
+
+def test_one_segment_is_the_anti_diagonal_sums():
+    """A span covering every ring difference (2 n - 1) leaves one segment whose
+    plane z is the sum over ra + rb = z."""
+    n = 6
+    rng = np.random.default_rng(4)
+    s = rng.integers(0, 100, size=(n * n, 1, 2, 1), dtype=np.int64)
+    out = oracle.span_mash(s, n, 2 * n - 1)
+    assert out.shape[0] == 2 * n - 1
+    for z in range(2 * n - 1):
+        want = sum(s[ra * n + (z - ra)] for ra in range(n) if 0 <= z - ra < n)
+        np.testing.assert_array_equal(out[z], want)
