@@ -987,6 +987,9 @@ def run_postproc(a):
     from paper_2509_05047_gb300 import build as B
     B.build()
     sc = W.scanner_signa()
+    if a.rings:   # profiling case: fewer rings, the same planes' layout
+        sc = W.Scanner(sc.radius, sc.n_crystals, a.rings, sc.ring_pitch, sc.module_t, sc.module_a,
+                       sc.e_lo, sc.e_hi, sc.n_tof, sc.tof_bin_mm, sc.tof_sigma_mm)
     ctx = psc.psc_create(0)
     s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
     a_id, o_id = psc.psc_acc_create(ctx, s_id), psc.psc_acc_create(ctx, s_id)
@@ -1005,7 +1008,10 @@ def run_postproc(a):
         "norm_sinogram_sigma4": (lambda: psc.psc_norm_sinogram(ctx, a_id, (4.0, 4.0, 4.0), out, sh), 32),
     }
     peaks, src = measured_peaks()
-    res = {"mode": "postproc", "workload": "paper-scale sinogram 2025x224x447x27 (5.47e9 bins), dense int64",
+    span_out = torch.empty((psc.psc_acc_span(ctx, a_id, 3),) + sc.shape[1:], dtype=torch.int64, device="cuda")
+    ops["span3"] = (lambda: psc.psc_acc_span(ctx, a_id, 3, span_out, sh), 8 + 8 * span_out.shape[0] / sc.n_planes)
+    res = {"mode": "postproc", "workload": f"paper-scale sinogram {sc.n_planes}x{sc.n_views}x{sc.n_rad}x{sc.n_tof} "
+                                           f"({sc.n_bins / 1e9:.2f}e9 bins), dense int64",
            "hbm_peak_gbs": peaks["hbm_gbs"], "ops": {}}
     for name, (f, bytes_per_bin) in ops.items():
         for _ in range(2):
