@@ -216,7 +216,7 @@ OPS_PER_HISTORY = 60
 # folded to one bin (the full 43.8 GB accumulator is too large to capture);
 # the traffic is the binned atomics and LUT misses, so it scales with the
 # histories of a launch
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.56e6 + 24.24e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.73e6 + 24.62e6) / 2e7  # ncu dram bytes of one 2e7-history launch (profiles/)
 # HBM bytes per bin of the smoothing finalize.  The method's own: the int64
 # accumulator read once and the FP64 estimate written once, plus the per-LOR
 # FP64 sensitivity (8 / n_tof per bin).  The three-pass design moves two FP32
@@ -955,13 +955,52 @@ def run_requests(a, served=None, chains=None, max_active=None):
 
         t_first, s_first = one_launch()
         t_again, s_again = one_launch()
+
+        # the same GPU step (zero, the tuned launch on the cached schedule, finalizes)
+        # captured once into a CUDA graph and replayed; the activity updates stay on
+        # the host, before each replay
+        batch_args = [psc.sim_args(r["seed"], 0, r["n"], scan[r["kind"]][0], pids[k], acc, lut=scan[r["kind"]][1])
+                      for r, k, acc in zip(mix, keys, accs)]
+
+        def gpu_step():
+            sh2 = torch.cuda.current_stream().cuda_stream
+            for acc in accs:
+                psc.psc_acc_zero(ctx, acc, sh2)
+            psc.psc_simulate_batch_tuned(ctx, batch_args, stream=sh2)
+            for r, acc in zip(mix, accs):
+                psc.psc_finalize(ctx, psc.finalize_args(acc, sens=scan[r["kind"]][2], sigma=sigma,
+                                                        scale=1.0 / r["n"]), out1, sh2)
+
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side, capture_error_mode="thread_local"):
+            gpu_step()
+        torch.cuda.synchronize()
+
+        def graph_step():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with ThreadPoolExecutor(16) as ex:
+                list(ex.map(lambda i: psc.psc_update_activity(ctx, pids[keys[i]], mix[i]["activity"]),
+                            range(len(mix))))
+            graph.replay()
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0
+
+        t_graph = min(graph_step() for _ in range(2))
+        del graph
         one = {"seconds": round(t_first, 4), "histories_per_s": total_h / t_first,
                "speedup_vs_plain": t_plain / t_first,
                "seconds_cached_schedule": round(t_again, 4), "histories_per_s_cached": total_h / t_again,
                "speedup_vs_plain_cached": t_plain / t_again,
+               "seconds_graph": round(t_graph, 4), "histories_per_s_graph": total_h / t_graph,
+               "speedup_vs_plain_graph": t_plain / t_graph,
                "schedule": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in s_first.items()},
                "note": "first call: the autotuner's probes run the first 6/48 of every budget with candidate "
-                       "schedules, the choice runs the rest; second call: the cached choice"}
+                       "schedules, the choice runs the rest; second call: the cached choice; graph: the GPU "
+                       "part captured once into a CUDA graph and replayed after the host's alias builds"}
     psc.psc_destroy(ctx)
     return {"mode": "served" if served else "batched", "requests": len(mix), "histories": total_h,
             "budget_scale": a.budget_scale,

@@ -28,6 +28,16 @@
  *   - Array layouts: voxels [nz][ny][nx]; LUT [apos][tpos][E][alpha][beta];
  *     sinograms [plane][view][radial][tof] with plane = ring_a * n_rings +
  *     ring_b; per-LOR inputs [plane][view][radial] apply to every TOF bin.
+ *   - Stream capture: psc_acc_zero, psc_acc_read / write, psc_simulate and
+ *     psc_simulate_batch (without stats), psc_simulate_batch_tuned (on a
+ *     request mix it has already tuned) and psc_finalize (psc_finalize_host
+ *     with copy_stream == stream) can be captured into a CUDA graph on one
+ *     stream, after the same calls have run once outside the capture (their
+ *     working buffers are allocated then; a capture cannot allocate or wait,
+ *     and such a call returns PSC_EINVAL).  Captured launches take their order
+ *     from the graph: replays are not ordered against the context's other
+ *     launches, or against psc_update_activity, except by the caller (for
+ *     example, one stream).
  */
 #ifndef PSC_H
 #define PSC_H

@@ -192,10 +192,25 @@ struct psc_ctx {
   std::map<std::vector<std::tuple<int, int, int>>, std::pair<psc::Sched, double>> tuned;
 };
 
+// True while stream s is being captured into a CUDA graph.  Calls captured
+// on one stream take their order from the graph: they skip the events that
+// order the context's shared buffers (slot buffer, smoothing scratch) and
+// phantoms across streams, and they cannot allocate or wait, so their
+// buffers must exist from an earlier call outside the capture.
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st == cudaStreamCaptureStatusActive;
+}
+
 // Debug builds: after a call's launches, wait for them and fail with
 // PSC_EDEVICE if a bounds check caught an index (the record is then cleared).
 static int debug_check(psc_ctx* ctx, cudaStream_t s, const char* what) {
 #if PSC_DEBUG
+  if (capturing(s)) return PSC_OK;  // checked when a launch outside a capture waits
   static const char* const kSites[] = {"self-test", "alias table", "voxel", "material id", "Rayleigh kappa",
                                        "LUT tap", "accumulator bin", "per-history output", "slot",
                                        "finalize bin", "finalize LOR factor", "smoothing column"};
@@ -1020,6 +1035,8 @@ static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_sta
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int block = sc_in.block ? sc_in.block : (n > 0 && args[0].block ? args[0].block : 512);
+  const bool cap = capturing(s);
+  if (cap && stats) return fail(PSC_EINVAL, "statistics wait for the stream: not in a stream capture");
   std::unique_lock<std::mutex> lk(ctx->stats_mu, std::defer_lock);
   unsigned long long* dstats = nullptr;
   if (stats) {
@@ -1074,6 +1091,8 @@ static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_sta
     std::lock_guard<std::mutex> cl(ctx->cold_mu);
     const size_t cold_bytes = sizeof(uint32_t) * transport_cold_words(grid, block);
     if (ctx->cold.bytes < cold_bytes) {
+      if (cap)
+        return fail(PSC_EINVAL, "the transport's slot buffer grows outside a capture: run the call once first");
       CK(cudaEventSynchronize(ctx->cold_done), "wait for the slot buffer's last user");
       if (ctx->cold.p) {
         cudaFree(ctx->cold.p);
@@ -1089,9 +1108,10 @@ static int batch_impl(psc_ctx* ctx, const psc_sim_args* args, int32_t n, psc_sta
       ctx->cold.bytes = cold_bytes;
     }
     bp.cold = (uint32_t*)ctx->cold.p;
-    CK(cudaStreamWaitEvent(s, ctx->cold_done, 0), "order slot buffer users");
+    if (!cap) CK(cudaStreamWaitEvent(s, ctx->cold_done, 0), "order slot buffer users");
     CK(launch_transport(bp, dt, grid, block, smem, s), "transport kernel launch");
     last_grid = grid;
+    if (cap) continue;  // a captured launch takes its order from the graph
     CK(cudaEventRecord(ctx->cold_done, s), "order slot buffer users");
     for (PhantomObj* ph : used) {  // activity updates wait for this launch
       std::lock_guard<std::mutex> ul(ph->use_mu);
@@ -1157,6 +1177,8 @@ int psc_simulate_batch_tuned(psc_ctx* ctx, const psc_sim_args* args, int32_t n, 
   double best_rate = 0.0;
   int probed = 0;
   auto cached = ctx->tuned.find(key);
+  if (cached == ctx->tuned.end() && capturing((cudaStream_t)stream))
+    return fail(PSC_EINVAL, "the autotuner's probes wait for the stream: tune this request mix outside a capture");
   if (cached != ctx->tuned.end()) {
     best = cached->second.first;
     best_rate = cached->second.second;
@@ -1281,6 +1303,7 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
   if (!std::isfinite(a->scale)) return fail(PSC_EINVAL, "scale must be finite");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
+  const bool cap = capturing(s);
   FinParams p;
   std::memset(&p, 0, sizeof p);
   const psc_scanner_desc& d = sc->desc;
@@ -1377,6 +1400,7 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
     p.norm = (const double*)norm->data.p;
     p.norm_per_lor = norm->per_lor;
     if (!norm->recip.p) {
+      if (cap) return fail(PSC_EINVAL, "the normalisation's reciprocal is made outside a capture: run the call once first");
       int rc;
       if ((rc = dev_alloc(ctx, norm->recip, sizeof(double) * norm->n))) return rc;
       norm->bytes += norm->recip.bytes;
@@ -1386,10 +1410,13 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
     p.rnorm = (const double*)norm->recip.p;
     p.norm32 = (const float*)norm->data32.p;
   }
+  if (cap && hc && hc->c != s)
+    return fail(PSC_EINVAL, "in a stream capture the copies to host memory run on the capturing stream");
   {
     std::lock_guard<std::mutex> lk(ctx->scratch_mu);
     const size_t need = sizeof(float) * (size_t)p.n_bins;
     if (ctx->scratch.bytes < need) {
+      if (cap) return fail(PSC_EINVAL, "the smoothing scratch grows outside a capture: run the call once first");
       cudaStreamSynchronize(s);
       cudaDeviceSynchronize();
       if (ctx->scratch.p) {
@@ -1406,7 +1433,7 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
       ctx->scratch.bytes = need;
     }
     p.scratch = (float*)ctx->scratch.p;
-    CK(cudaStreamWaitEvent(s, ctx->scratch_done, 0), "order scratch users");
+    if (!cap) CK(cudaStreamWaitEvent(s, ctx->scratch_done, 0), "order scratch users");
     if (!hc) {
       CK(launch_finalize(p, ctx->sms, s), "finalize");
     } else {
@@ -1418,7 +1445,7 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
       });
       if (rc) return rc;
     }
-    CK(cudaEventRecord(ctx->scratch_done, s), "order scratch users");
+    if (!cap) CK(cudaEventRecord(ctx->scratch_done, s), "order scratch users");
   }
   return PSC_OK;
 }
