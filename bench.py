@@ -192,6 +192,33 @@ def huge_page_gb(ptr):
     return None
 
 
+def host_memory_state():
+    """Host memory facts that bear on device-to-host copies: the cgroup's
+    limit and use, this process's resident set, and the kernel's compaction,
+    THP and reclaim counters (to difference across the end-to-end leg)."""
+    out = {}
+    for k, path in (("cgroup_max_gb", "/sys/fs/cgroup/memory.max"), ("cgroup_current_gb", "/sys/fs/cgroup/memory.current")):
+        try:
+            v = open(path).read().strip()
+            out[k] = None if v == "max" else round(int(v) / 1e9, 2)
+        except (OSError, ValueError):
+            pass
+    try:
+        for line in open("/proc/self/status"):
+            if line.startswith("VmRSS:"):
+                out["rss_gb"] = round(int(line.split()[1]) * 1024 / 1e9, 2)
+    except OSError:
+        pass
+    keys = ("compact_stall", "compact_fail", "thp_fault_alloc", "thp_fault_fallback", "thp_collapse_alloc",
+            "pgscan_direct", "pgsteal_direct", "pgmajfault")
+    try:
+        vm = dict(line.split() for line in open("/proc/vmstat"))
+        out["vmstat"] = {k: int(vm[k]) for k in keys if k in vm}
+    except (OSError, ValueError):
+        pass
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -415,6 +442,7 @@ def run_native(a):
     # read-back still speeds up.
     e2e = None
     if not a.no_e2e and rank == 0:
+        mem_before = host_memory_state()
         host_out = psc.host_tensor(sc.shape, torch.float64)   # page-locked, huge pages
         act = np.ascontiguousarray(ph.activity, dtype=np.float32)
         outs = [out, torch.empty_like(out)]
@@ -463,6 +491,7 @@ def run_native(a):
         nbytes = int(out.numel() * 8)
         e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": int(act.nbytes),
                "host_buffer_huge_page_gb": huge_page_gb(host_out.data_ptr()),
+               "host_memory": {"before": mem_before, "after": host_memory_state()},
                "d2h_bytes_per_step": nbytes, "steps": k, "warmup": n_warm,
                "api": "psc_update_activity + psc_acc_zero + psc_simulate + psc_finalize_host (C ABI)",
                "pipelined": "read-back of step i overlaps the smoothing of step i and step i+1 "
