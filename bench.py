@@ -210,7 +210,15 @@ def host_memory_state():
     except OSError:
         pass
     keys = ("compact_stall", "compact_fail", "thp_fault_alloc", "thp_fault_fallback", "thp_collapse_alloc",
-            "pgscan_direct", "pgsteal_direct", "pgmajfault")
+            "thp_split_page", "thp_split_pmd", "thp_migration_split", "thp_migration_fail", "pgmigrate_success",
+            "pgmigrate_fail", "pgscan_direct", "pgsteal_direct", "pgmajfault")
+    try:
+        for line in open("/proc/meminfo"):
+            name, val = line.split(":", 1)
+            if name in ("CmaTotal", "CmaFree", "MemFree", "AnonHugePages"):
+                out[name] = round(int(val.split()[0]) * 1024 / 1e9, 2)
+    except (OSError, ValueError):
+        pass
     try:
         vm = dict(line.split() for line in open("/proc/vmstat"))
         out["vmstat"] = {k: int(vm[k]) for k in keys if k in vm}
@@ -452,6 +460,7 @@ def run_native(a):
     if not a.no_e2e and rank == 0:
         mem_before = host_memory_state()
         host_out = psc.host_tensor(sc.shape, torch.float64)   # page-locked, huge pages
+        mem_alloc = dict(host_memory_state(), buffer_huge_page_gb=huge_page_gb(host_out.data_ptr()))
         act = np.ascontiguousarray(ph.activity, dtype=np.float32)
         outs = [out, torch.empty_like(out)]
         copy = torch.cuda.Stream(dev)
@@ -499,7 +508,7 @@ def run_native(a):
         nbytes = int(out.numel() * 8)
         e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": int(act.nbytes),
                "host_buffer_huge_page_gb": huge_page_gb(host_out.data_ptr()),
-               "host_memory": {"before": mem_before, "after": host_memory_state()},
+               "host_memory": {"before": mem_before, "after_alloc": mem_alloc, "after": host_memory_state()},
                "d2h_bytes_per_step": nbytes, "steps": k, "warmup": n_warm,
                "api": "psc_update_activity + psc_acc_zero + psc_simulate + psc_finalize_host (C ABI)",
                "pipelined": "read-back of step i overlaps the smoothing of step i and step i+1 "

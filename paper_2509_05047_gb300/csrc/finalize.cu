@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // where there is one: its factors would otherwise hold registers)
 template <int KT, bool kDivide, bool kNorm>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
-  constexpr int NB = KT >= 0 ? 4 : kNb<KT>;
+  constexpr int NB = KT >= 0 ? 2 : kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;

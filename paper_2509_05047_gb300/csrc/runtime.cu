@@ -5,6 +5,7 @@
 // LUTs, sensitivity / normalisation sinograms and int64 accumulators.  Calls
 // validate their arguments, never throw across the ABI, and enqueue kernels
 // on the caller's stream.
+#include <cerrno>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -515,9 +516,26 @@ int psc_host_alloc(uint64_t bytes, void** ptr) {
   const long pg = sysconf(_SC_PAGESIZE);
   const size_t step = pg > 0 ? (size_t)pg : 4096;
   for (size_t i = 0; i < len; i += step) p[i] = 0;  // fault in now, as huge pages where possible
-  // where a fault found no free huge page (fragmented memory), collapse the
-  // range into huge pages now (Linux 6.1+; ignored where unsupported)
-  madvise(p, len, kMadvCollapse);
+  // where a fault found no free huge page (fragmented memory), collapse each
+  // huge-page block now (Linux 6.1+): a block that fails is released and
+  // faulted in again, then collapsed once more.  A registered buffer with
+  // base pages scattered through it read back at a quarter of the host
+  // link's rate in measurements; where the kernel cannot collapse, the
+  // buffer stays as faulted.
+  for (size_t off = 0; off < len; off += hp) {
+    char* b = p + off;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      if (madvise(b, hp, kMadvCollapse) == 0) break;
+      if (errno == EINVAL) {  // no MADV_COLLAPSE in this kernel
+        off = len;
+        break;
+      }
+      if (attempt == 1) {     // give the block's memory back and fault it in again
+        madvise(b, hp, MADV_DONTNEED);
+        for (size_t i = 0; i < hp; i += step) b[i] = 0;
+      }
+    }
+  }
   const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
   if (e != cudaSuccess) {
     cudaGetLastError();

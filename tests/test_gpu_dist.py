@@ -94,3 +94,39 @@ def test_two_ranks_equal_one_process(tmp_path):
         np.testing.assert_array_equal(est[planes], ref[planes])
     assert total == n and sorted(seen) == list(range(sc.n_planes))
     assert np.count_nonzero(ref) > 0
+
+
+def test_acc_wrap_checks_its_memory():
+    """psc_acc_wrap takes 8-byte-aligned device memory of the context's device
+    only, and a wrapped accumulator is not freed by psc_unload."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2509_05047_gb300 as psc
+    import workloads as W
+    from paper_2509_05047_gb300 import build
+    build.build()
+    sc = W.scanner_small(n_crystals=16, n_rings=4, n_tof=5)
+    ctx = psc.psc_create(0)
+    try:
+        s_id = psc.psc_load_scanner(ctx, psc.scanner_desc(sc))
+        t = torch.zeros(sc.n_bins + 1, dtype=torch.int64, device="cuda")
+        before = psc.psc_resident_bytes(ctx)
+        a = psc.psc_acc_wrap(ctx, s_id, t)
+        assert psc.psc_resident_bytes(ctx) == before        # not counted against the budget
+        t[:sc.n_bins] = 7
+        out = torch.empty(sc.n_bins, dtype=torch.int64, device="cuda")
+        psc.psc_acc_read(ctx, a, out, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert int(out.sum()) == 7 * sc.n_bins
+        psc.psc_unload(ctx, a)
+        t.fill_(1)                                          # still the caller's memory
+        torch.cuda.synchronize()
+        odd = t.view(torch.uint8)[4:4 + 8 * sc.n_bins]
+        for bad in (odd, t.cpu(), None):
+            with pytest.raises((psc.PscError, TypeError, AttributeError)) as e:
+                psc.psc_acc_wrap(ctx, s_id, bad)
+            if isinstance(e.value, psc.PscError):
+                assert e.value.code == psc.PSC_EINVAL
+    finally:
+        psc.psc_destroy(ctx)

@@ -152,6 +152,38 @@ def test_finalize_to_host_equals_device_finalize(small, sigma, same_stream):
     assert torch.equal(work, ref)
 
 
+@pytest.mark.parametrize("segments", [(0, 17), (3, 9), (8, 9), (16, 17)])
+@pytest.mark.parametrize("sigma", [None, (2.0, 1.5, 2.0)])
+def test_segment_range_finalize_to_host(small, segments, sigma):
+    """A finalize restricted to ring-difference segments [lo, hi) gives, on
+    those segments' planes, exactly the full finalize's values, on the
+    device and copied to host memory (the copies then cover only those
+    planes: rows ra (n + 1) + d of the layout)."""
+    torch = small.torch
+    nr = small.sc.n_rings
+    kw = dict(sens=small.ids["sens_lor"], sigma=sigma, scale=1.5)
+    full = small.run(**kw).cpu().numpy()
+    lo, hi = segments
+    planes = [ra * nr + rb for ra in range(nr) for rb in range(nr) if lo <= rb - ra + nr - 1 < hi]
+    dev = small.run(segments=segments, **kw).cpu().numpy()
+    np.testing.assert_array_equal(dev[planes], full[planes])
+    host = psc.host_tensor(small.sc.shape, torch.float64)
+    host.fill_(float("nan"))
+    work = torch.empty(small.sc.shape, dtype=torch.float64, device="cuda")
+    copy = torch.cuda.Stream()
+    stream = torch.cuda.current_stream()
+    psc.psc_finalize_host(small.ctx, psc.finalize_args(small.a_id, segments=segments, **kw), work, host,
+                          stream.cuda_stream, copy.cuda_stream)
+    copy.synchronize()
+    h = host.numpy()
+    np.testing.assert_array_equal(h[planes], full[planes])
+    others = np.setdiff1d(np.arange(small.sc.n_planes), planes)
+    assert np.isnan(h[others]).all()          # nothing else is copied
+    with pytest.raises(psc.PscError) as e:
+        small.run(segments=(5, 40), **kw)
+    assert e.value.code == psc.PSC_EINVAL
+
+
 def test_smoothing_conserves_mass_and_delta(small):
     acc = np.zeros(small.sc.shape, np.int64)
     acc[40, 7, 16, 2] = 1 << 32
