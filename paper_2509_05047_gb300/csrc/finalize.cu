@@ -160,8 +160,14 @@ __device__ __forceinline__ double dmul(double a, double b) {
   const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
   const unsigned long long sign = (ua ^ ub) & (1ull << 63);
   const int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
-  if (((ua << 1) == 0) || ((ub << 1) == 0)) return __longlong_as_double((long long)sign);
-  if (ea == 0 || eb == 0 || ea == 0x7ff || eb == 0x7ff) return hw_dmul(a, b);
+  // zero, subnormal, infinite and NaN operands: one range test on the exponent
+  // fields first (a zero test on an FP64 operand's bits can be compiled to an
+  // FP64 compare, which this keeps off the common path)
+  if ((unsigned)(ea - 1) >= 0x7feu || (unsigned)(eb - 1) >= 0x7feu) {
+    if (((ua << 1) == 0 && eb != 0x7ff) || ((ub << 1) == 0 && ea != 0x7ff))
+      return __longlong_as_double((long long)sign);
+    return hw_dmul(a, b);
+  }
   const unsigned long long ma = (ua & kMant52) | (1ull << 52), mb = (ub & kMant52) | (1ull << 52);
   // ma * mb in [2^104, 2^106): top 64 bits of (ma * mb) << 22, sticky below
   const unsigned long long hi = __umul64hi(ma << 11, mb << 11);
@@ -174,37 +180,52 @@ __device__ __forceinline__ double dmul(double a, double b) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (m & kMant52)));
 }
 
-// (double)y * f, rounded to nearest even, for a float y and a double f: the
-// 24-bit by 53-bit significand product P in [2^75, 2^77) from two 32 x 32 ->
-// 64-bit products; P >> 13 (or >> 12 when P < 2^76) puts the leading bit at
-// bit 63, the 11 bits below the kept 53 decide the rounding with the sticky
-// bit of the rest, and the rounded significand (hidden bit included) is
-// added to the exponent field, so a rounding carry moves into the exponent
-// (and past the largest finite value to infinity) as IEEE rounding does.
-// Zero operands are handled inline; subnormal, infinite and NaN operands and
-// results outside the normal range go to the FP64 hardware.
+// (double)y * f, rounded to nearest even, for a float y and a double f, in
+// 32-bit integer words: the 24-bit by 53-bit significand product, scaled by
+// 2^8, from the low and high halves of four 32 x 32-bit products (fewer
+// instructions than two 64-bit products, measured); the leading bit is normalised to bit
+// 84 of the 96-bit value, the top 53 bits are the significand and the low
+// word decides the rounding (ties to even); the rounded significand (hidden
+// bit included) is added to the exponent field, so a rounding carry moves
+// into the exponent (and past the largest finite value to infinity) as IEEE
+// rounding does.  A zero y is handled inline; other zero, subnormal, infinite
+// and NaN operands and results outside the normal range go to the FP64
+// hardware.
 __device__ __forceinline__ double mul_f32_f64(float y, double f) {
   const unsigned by = (unsigned)__float_as_int(y);
   const unsigned long long uf = (unsigned long long)__double_as_longlong(f);
   const unsigned fhi = (unsigned)(uf >> 32);
   const unsigned ey = (by >> 23) & 0xffu, ef = (fhi >> 20) & 0x7ffu;
   const unsigned long long sign = (unsigned long long)((by ^ fhi) & 0x80000000u) << 32;
-  if (((by << 1) == 0u && ef != 0x7ffu) || ((uf << 1) == 0ull && ey != 0xffu))
-    return __longlong_as_double((long long)sign);
-  if (ey - 1u >= 254u || ef - 1u >= 0x7feu) return hw_dmul(hw_f32_to_f64(y), f);
-  const unsigned my = (by & 0x7fffffu) | 0x800000u;
-  const unsigned long long t0 = (unsigned long long)my * (unsigned)uf;                      // < 2^56
-  const unsigned long long t1 = (unsigned long long)my * ((fhi & 0xfffffu) | 0x100000u);   // < 2^45
-  const unsigned long long hi = (t0 >> 13) + (t1 << 19);                                    // P >> 13
-  const unsigned top = (unsigned)(hi >> 63), sh = top ^ 1u;
-  const unsigned long long g = (hi << sh) | ((t0 >> 12) & (unsigned long long)sh);
-  const bool sticky = ((unsigned)t0 & (0x1fffu >> sh)) != 0u;
-  const unsigned long long q = g >> 11;
-  const unsigned rem = (unsigned)g & 0x7ffu;
-  const unsigned up = (rem > 0x400u || (rem == 0x400u && (sticky || (q & 1ull)))) ? 1u : 0u;
+  // zero, subnormal, infinite and NaN operands: one range test on the two
+  // exponent fields (integer compares; a zero test on the FP64 operand's bits
+  // can be compiled to an FP64 compare); y = 0 with a finite f is the common
+  // case among them (bins the smoothing leaves empty)
+  if (ey - 1u >= 254u || ef - 1u >= 0x7feu) {
+    if ((by << 1) == 0u && ef != 0x7ffu) return __longlong_as_double((long long)sign);
+    return hw_dmul(hw_f32_to_f64(y), f);
+  }
+  // P 2^8 = my 2^8 x (fh 2^32 + fl) as three 32-bit words w2:w1:w0 from 32 x 32-bit
+  // products (low and high halves); P 2^8 in [2^83, 2^85), its leading bit at w2 bit 20
+  // (top = 1) or 19 (shifted up by one).  The 53-bit significand is then w2:w1 and w0
+  // holds the rounding bits.
+  const unsigned m = (by << 8) | 0x80000000u;
+  const unsigned fl = (unsigned)uf, fh = (fhi & 0xfffffu) | 0x100000u;
+  const unsigned a0 = m * fl, a1 = __umulhi(m, fl), b0 = m * fh, b1 = __umulhi(m, fh);
+  unsigned w1 = b0 + a1;
+  unsigned w2 = b1 + (w1 < a1 ? 1u : 0u), w0 = a0;
+  const unsigned top = w2 >> 20;
+  if (!top) {
+    w2 = __funnelshift_l(w1, w2, 1);
+    w1 = __funnelshift_l(w0, w1, 1);
+    w0 <<= 1;
+  }
+  const unsigned up = (w0 > 0x80000000u || (w0 == 0x80000000u && (w1 & 1u))) ? 1u : 0u;
   const int e = (int)ey - 127 + (int)ef + (int)top;  // (ey - 127) + (ef - 1023) + 1023, +1 when P >= 2^76
   if (e <= 0 || e >= 0x7ff) return hw_dmul(hw_f32_to_f64(y), f);
-  return __longlong_as_double((long long)(sign | (((unsigned long long)(e - 1) << 52) + q + up)));
+  const unsigned lo = w1 + up;
+  const unsigned hiw = (((unsigned)(e - 1) << 20) + w2 + (lo < up ? 1u : 0u)) | (unsigned)(sign >> 32);
+  return __hiloint2double((int)hiw, (int)lo);
 }
 
 // The j-th plane a launch covers: plane j itself, or, when the launch is

@@ -290,3 +290,35 @@ def test_fp64_products_round_like_ieee(small):
         out = small.run(sens=s_id, scale=scale).cpu().numpy()
         np.testing.assert_array_equal(out, oracle.finalize(acc, small.sc.n_rings, sens=sens, scale=scale))
     small.write_acc(small.acc)
+
+
+def test_smoothed_epilogue_rounds_ties_like_ieee(small):
+    """The smoothed path's FP64 product of the FP32 value y and the FP64
+    sensitivity, on operands whose exact products sit on rounding ties: with
+    zero-width kernels and scale 2^32 the FP32 passes carry y = acc exactly
+    (acc < 2^24), and y (24-bit odd significand) times a sensitivity with an
+    odd 30-bit significand is an odd 54-bit integer times a power of two,
+    halfway between two FP64 values.  Random exponents put the product's
+    leading bit on both sides of the significand boundary, and plain random
+    operands are mixed in; numpy's IEEE product is the expected value."""
+    rng = np.random.default_rng(23)
+    sc = small.sc
+    s_m = rng.integers((1 << 29) + 1, 1 << 30, size=sc.lor_shape) | 1
+    sens = s_m.astype(np.float64) * np.exp2(rng.integers(-20, 21, size=sc.lor_shape) - 30.0)
+    lo = np.maximum(1 << 23, -(-(1 << 53) // s_m))               # y s_m >= 2^53
+    hi = np.minimum((1 << 24) - 1, ((1 << 54) - 1) // s_m)        # y s_m < 2^54
+    assert bool((lo <= hi).all())
+    t = sc.n_tof
+    y = rng.integers(lo[..., None].repeat(t, -1), hi[..., None].repeat(t, -1) + 1) | 1
+    y = np.minimum(y, hi[..., None]) | 1
+    y = np.where(y > hi[..., None], y - 2, y)
+    plain = rng.uniform(size=sc.shape) < 0.25
+    y[plain] = rng.integers(1, 1 << 24, size=int(plain.sum()))
+    acc = y.astype(np.int64)
+    prod = (acc.astype(object) * s_m[..., None].astype(object))[~plain]
+    assert all(54 <= int(p).bit_length() <= 55 for p in prod[:1000])
+    small.write_acc(acc)
+    s_id = small.sino(sens, True)
+    out = small.run(sens=s_id, sigma=(0.0, 0.0, 0.0), scale=2.0**32).cpu().numpy()
+    np.testing.assert_array_equal(out, acc.astype(np.float64) * sens[..., None])
+    small.write_acc(small.acc)
