@@ -415,6 +415,101 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
   slide_any<KT, NB>(src, I, V, P.K[1], P.g[1], cvt, store);
 }
 
+// The epilogue of one output: the FP32 smoothed value y in FP64 (exactly
+// widened, times the FP64 reciprocal of the normalisation fr, times the FP64
+// sensitivity fs, each product rounded to nearest, on the integer pipes), or
+// for the normalisation sinogram (kDivide) y over the scaled input bin qa,
+// 0 where qa is 0.
+template <bool kDivide, bool kNorm>
+__device__ __forceinline__ double axial_epilogue(float y, long long qa, double fr, double fs, bool use_sens,
+                                                 float cf) {
+  if (kDivide) return f32_to_f64(qa != 0 ? y / (i64_to_f32(qa) * cf) : 0.0f);
+  if (kNorm) {
+    const double x = mul_f32_f64(y, fr);
+    return use_sens ? dmul(x, fs) : x;
+  }
+  return use_sens ? mul_f32_f64(y, fs) : f32_to_f64(y);
+}
+
+// One axial column of an instantiated radius KT: the sliding window of slide
+// with 2-output steps, written out for this pass.  Row, output and factor
+// addresses advance by running pointers (one 64-bit add per step each); for
+// columns of at least KT planes the first window's reflected rows are copies
+// of rows 0 .. KT - 1, so it takes KT loads instead of 2 KT.  Same loads (up
+// to those copies), same FMA chains and same outputs as slide.
+template <int KT, bool kDivide, bool kNorm>
+__device__ __forceinline__ void axial_column(const FinParams& P, long long bin0, long long lor0, long long bin_step,
+                                             long long lor_step, int L) {
+  constexpr int NB = 2;
+  const Weights& g = P.g[2];
+  const float* __restrict__ src = P.scratch + bin0;
+  float w[2 * KT + NB];
+  if (L >= KT) {
+#pragma unroll
+    for (int r = 0; r < KT; ++r) {  // row r, and row -1 - r reflected onto it
+      const float x = __ldg(src + r * bin_step);
+      w[KT + r] = x;
+      w[KT - 1 - r] = x;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) w[j] = __ldg(src + reflect(j - KT, L) * bin_step);
+  }
+  const bool use_sens = !P.sens_first && P.sens;
+  const float cf = (float)P.c;
+  const long long step2 = NB * bin_step;
+  const float* nxt = src + KT * bin_step;  // row o0 + KT
+  double* dst = P.out + bin0;
+  const long long* ap = P.acc + bin0;
+  const long long rs = P.norm_per_lor ? lor_step : bin_step, ss = P.sens_per_lor ? lor_step : bin_step;
+  const double* rp = kNorm ? P.rnorm + (P.norm_per_lor ? lor0 : bin0) : nullptr;
+  const double* sp = use_sens ? P.sens + (P.sens_per_lor ? lor0 : bin0) : nullptr;
+  for (int o0 = 0; o0 < L; o0 += NB) {
+    float r0, r1;
+    if (o0 + KT + NB <= L) {
+      r0 = __ldg(nxt);
+      r1 = __ldg(nxt + bin_step);
+    } else {
+      r0 = __ldg(src + reflect(o0 + KT, L) * bin_step);
+      r1 = __ldg(src + reflect(o0 + KT + 1, L) * bin_step);
+    }
+    nxt += step2;
+    w[2 * KT] = r0;
+    w[2 * KT + 1] = r1;
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j <= 2 * KT; ++j) {
+      s0 = fmaf(g[j], w[j], s0);
+      s1 = fmaf(g[j], w[j + 1], s1);
+    }
+    const bool two = o0 + 1 < L;
+    // the step's factors, loaded before its outputs are stored
+    long long qa0 = 0, qa1 = 0;
+    double fr0 = 1.0, fr1 = 1.0, fs0 = 1.0, fs1 = 1.0;
+    if (kDivide) {
+      qa0 = __ldg(ap);
+      if (two) qa1 = __ldg(ap + bin_step);
+      ap += step2;
+    } else {
+      if (kNorm) {
+        fr0 = __ldg(rp);
+        if (two) fr1 = __ldg(rp + rs);
+        rp += NB * rs;
+      }
+      if (use_sens) {
+        fs0 = __ldg(sp);
+        if (two) fs1 = __ldg(sp + ss);
+        sp += NB * ss;
+      }
+    }
+    dst[0] = axial_epilogue<kDivide, kNorm>(s0, qa0, fr0, fs0, use_sens, cf);
+    if (two) dst[bin_step] = axial_epilogue<kDivide, kNorm>(s1, qa1, fr1, fs1, use_sens, cf);
+    dst += step2;
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) w[j] = w[NB + j];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass C: axial within a ring-difference segment, then the epilogue.
 // grid (ceil(R T / 256), segments x V); a thread owns the column (segment,
@@ -426,7 +521,6 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_view_kernel(const __gri
 // where there is one: its factors would otherwise hold registers)
 template <int KT, bool kDivide, bool kNorm>
 __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
-  constexpr int NB = KT >= 0 ? 2 : kNb<KT>;
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
@@ -449,47 +543,28 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __gr
       dbg_idx(P.dbg, kSiteFinLor, lor0 + (L - 1) * lor_step, P.n_bins / P.T) != lor0 + (L - 1) * lor_step)
     return;
 #endif
-  auto cvt = [](float x, int) { return x; };
-  const bool use_sens = !P.sens_first && P.sens;
-  // the epilogue in FP64: the smoothed FP32 value widened exactly, times the
-  // FP64 reciprocal of the normalisation, times the FP64 sensitivity, each
-  // product rounded to nearest (on the integer pipes).  The factor loads of
-  // a step are issued before any output is stored.
-  const float cf = (float)P.c;
-  auto store = [&](int k0, const float (&o)[NB]) {
-    const long long b0 = bin0 + k0 * bin_step, l0 = lor0 + k0 * lor_step;
-    double fr[kNorm ? NB : 1], fs[NB];
-    long long qa[NB];
+  if constexpr (KT >= 0) {
+    axial_column<KT, kDivide, kNorm>(P, bin0, lor0, bin_step, lor_step, L);
+  } else {
+    // radii above the largest instantiated window: one load per tap
+    constexpr int NB = kNb<KT>;
+    const bool use_sens = !P.sens_first && P.sens;
+    const float cf = (float)P.c;
+    auto cvt = [](float x, int) { return x; };
+    auto store = [&](int k0, const float (&o)[NB]) {
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const long long bin = b0 + q * bin_step, lor = l0 + q * lor_step;
-      const bool in = k0 + q < L;
-      if (kDivide) {
-        qa[q] = in ? __ldg(P.acc + bin) : 0;
-      } else {
-        if constexpr (kNorm) fr[q] = in ? at(P.rnorm, P.norm_per_lor ? lor : bin) : 1.0;
-        fs[q] = use_sens && in ? at(P.sens, P.sens_per_lor ? lor : bin) : 1.0;
+      for (int q = 0; q < NB; ++q) {
+        const int k = k0 + q;
+        if (k >= L) break;
+        const long long bin = bin0 + k * bin_step, lor = lor0 + k * lor_step;
+        const long long qa = kDivide ? __ldg(P.acc + bin) : 0;
+        const double fr = kNorm ? at(P.rnorm, P.norm_per_lor ? lor : bin) : 1.0;
+        const double fs = use_sens && !kDivide ? at(P.sens, P.sens_per_lor ? lor : bin) : 1.0;
+        P.out[bin] = axial_epilogue<kDivide, kNorm>(o[q], qa, fr, fs, use_sens, cf);
       }
-    }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      if (k0 + q >= L) break;
-      const float y = o[q];
-      double x;
-      if (kDivide) {
-        x = f32_to_f64(qa[q] != 0 ? y / (i64_to_f32(qa[q]) * cf) : 0.0f);
-      } else if (kNorm) {
-        x = mul_f32_f64(y, fr[kNorm ? q : 0]);
-        if (use_sens) x = dmul(x, fs[q]);
-      } else if (use_sens) {
-        x = mul_f32_f64(y, fs[q]);
-      } else {
-        x = f32_to_f64(y);
-      }
-      P.out[b0 + q * bin_step] = x;
-    }
-  };
-  slide_any<KT, NB>(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
+    };
+    slide_generic(P.scratch + bin0, bin_step, L, P.K[2], P.g[2], cvt, store);
+  }
 }
 
 // reciprocal of a normalisation sinogram, 0 where it is 0: FP64 (r) and/or
