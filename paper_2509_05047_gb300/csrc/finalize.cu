@@ -431,9 +431,27 @@ __device__ __forceinline__ double axial_epilogue(float y, long long qa, double f
   return use_sens ? mul_f32_f64(y, fs) : f32_to_f64(y);
 }
 
+// The same epilogue on the FP64 hardware: y widened (exact) and multiplied by
+// correctly rounded FP64 instructions, so the same bits as axial_epilogue.
+// GB300's FP64 pipe retires about 2 operations per clock per SM; the axial
+// pass sends one output of each 2-output step here and the other through the
+// integer-pipe product, which splits the epilogue between the two pipes.
+template <bool kDivide, bool kNorm>
+__device__ __forceinline__ double axial_epilogue_fp64(float y, long long qa, double fr, double fs, bool use_sens,
+                                                      float cf) {
+  if (kDivide) return (double)(qa != 0 ? y / (i64_to_f32(qa) * cf) : 0.0f);
+  if (kNorm) {
+    const double x = (double)y * fr;
+    return use_sens ? x * fs : x;
+  }
+  return use_sens ? (double)y * fs : (double)y;
+}
+
 // One axial column of an instantiated radius KT: the sliding window of slide
-// with 2-output steps, written out for this pass.  Row, output and factor
-// addresses advance by running pointers (one 64-bit add per step each); for
+// with 2-output steps, written out for this pass.  The step's first output
+// takes the integer-pipe epilogue and its second the FP64-pipe one.  Row,
+// output and factor addresses advance by running pointers (one 64-bit add
+// per step each); for
 // columns of at least KT planes the first window's reflected rows are copies
 // of rows 0 .. KT - 1, so it takes KT loads instead of 2 KT.  Same loads (up
 // to those copies), same FMA chains and same outputs as slide.
@@ -503,7 +521,7 @@ __device__ __forceinline__ void axial_column(const FinParams& P, long long bin0,
       }
     }
     dst[0] = axial_epilogue<kDivide, kNorm>(s0, qa0, fr0, fs0, use_sens, cf);
-    if (two) dst[bin_step] = axial_epilogue<kDivide, kNorm>(s1, qa1, fr1, fs1, use_sens, cf);
+    if (two) dst[bin_step] = axial_epilogue_fp64<kDivide, kNorm>(s1, qa1, fr1, fs1, use_sens, cf);
     dst += step2;
 #pragma unroll
     for (int j = 0; j < 2 * KT; ++j) w[j] = w[NB + j];
