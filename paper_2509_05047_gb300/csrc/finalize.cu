@@ -537,8 +537,15 @@ __device__ __forceinline__ void axial_column(const FinParams& P, long long bin0,
 // 0 where the input is 0 (the smoothing-normalisation sinogram)
 // kNorm: a normalisation reciprocal multiplies the output (compiled in only
 // where there is one: its factors would otherwise hold registers)
+// resident CTAs per SM asked of the compiler for windows up to radius 8: the
+// pass waits on memory, and 6 CTAs (48 warps) outweigh a 12-byte spill
+// (measured); with a normalisation 4 (no spill); wider windows keep their
+// registers
+template <int KT, bool kNorm>
+constexpr int kAxialMinCtas = KT >= 0 && KT <= 8 ? (kNorm ? 4 : 6) : 1;
+
 template <int KT, bool kDivide, bool kNorm>
-__global__ void __launch_bounds__(kSmoothThreads) smooth_axial_kernel(const __grid_constant__ FinParams P) {
+__global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>)) smooth_axial_kernel(const __grid_constant__ FinParams P) {
   const int I = P.R * P.T;
   const int i = blockIdx.x * kSmoothThreads + threadIdx.x;
   if (i >= I) return;
