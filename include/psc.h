@@ -308,7 +308,12 @@ int psc_simulate_batch_tuned(psc_ctx* ctx, const psc_sim_args* args, int32_t n, 
  * x sens (Sec. 2.2.4, 2.3.2), written to out (device f64, sinogram size).
  * With smoothing, out also serves as the first pass's FP32 working buffer
  * until the last pass overwrites it.  Smoothing supports up to 255 rings
- * and (2 n_rings - 1) * n_crystals / 2 <= 65535, else PSC_EINVAL. */
+ * and (2 n_rings - 1) * n_crystals / 2 <= 65535, else PSC_EINVAL.  Where the
+ * shape allows, the axial pass stages its tiles in shared memory by TMA
+ * copies whose waits are bounded; a wait that runs out stops that pass (its
+ * estimate is then incomplete) and the next finalize call on the context
+ * returns PSC_EDEVICE.  PSC_AXIAL_TMA=0 in the environment switches the
+ * staging off (same results). */
 int psc_finalize(psc_ctx* ctx, const psc_finalize_args* args, double* out /* device */,
                  psc_stream stream);
 /* The scatter estimate of psc_finalize delivered to host memory (the

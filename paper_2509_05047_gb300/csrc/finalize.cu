@@ -30,6 +30,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
+#include <type_traits>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "psc.h"
 #include "psc_internal.h"
@@ -544,6 +549,187 @@ __device__ __forceinline__ void axial_column(const FinParams& P, long long bin0,
 template <int KT, bool kNorm>
 constexpr int kAxialMinCtas = KT >= 0 && KT <= 8 ? (kNorm ? 4 : 6) : 1;
 
+// ---------------------------------------------------------------------------
+// pass C with TMA-staged tiles.  The pass is bound by memory latency when
+// each thread loads its column's rows one step at a time.  Here a CTA owns
+// the tile of 256 consecutive bins of a plane (a chunk of the plane's J bins;
+// the axial pass treats every bin alike) over the L planes of one segment:
+// one thread issues L row copies (cp.async.bulk.tensor, 1 KB each) into
+// shared memory at once, in groups of kTmaRows rows that complete on their
+// own mbarrier, and every thread slides down its column in shared memory,
+// waiting for a group only when its first row is needed.  Outputs, factors
+// and arithmetic are those of axial_column (bit-identical results).
+// grid (ceil(J / 256), segments); shared memory: the launch's longest segment, in KB.
+// ---------------------------------------------------------------------------
+constexpr int kTmaRows = 8;           // rows per mbarrier group
+constexpr int kTmaMaxRings = 96;      // tiles of at most 96 rows (96 KB of shared memory)
+constexpr int kTmaShortRows = 36;     // segments up to 36 planes: 6 CTAs of 36 KB tiles per SM
+constexpr long kTmaSpinLimit = 1L << 24;  // bounded wait: then the status word is set and the CTA stops
+
+__device__ __forceinline__ unsigned smem_u32(const void* q) { return (unsigned)__cvta_generic_to_shared(q); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_done(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// one box of the 2D map (x: bin in the plane, y: plane) into shared memory,
+// completing on bar
+__device__ __forceinline__ void tma_row(float* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int KT, bool kDivide, bool kNorm>
+__global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
+    smooth_axial_tma_kernel(const __grid_constant__ FinParams P, const __grid_constant__ CUtensorMap map) {
+  extern __shared__ __align__(128) float tile[];  // [L][kSmoothThreads]
+  __shared__ __align__(8) unsigned long long bar[kTmaMaxRings / kTmaRows];
+  constexpr int NB = 2;
+  const int nr = P.n_rings;
+  const int seg = P.seg0 + (int)blockIdx.y;
+  const int d = seg - (nr - 1);  // ring difference rb - ra
+  const int L = nr - abs(d);
+  const long long p0 = (long long)max(0, -d) * (nr + 1) + d;
+  const long long J = (long long)P.V * P.R * P.T;
+  const int x0 = (int)blockIdx.x * kSmoothThreads;  // the chunk's first bin in a plane
+  const int ng = (L + kTmaRows - 1) / kTmaRows;
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < ng; ++g) mbar_init(&bar[g], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int g = 0; g < ng; ++g) {
+      const int k0 = g * kTmaRows, k1 = min(L, k0 + kTmaRows);
+      mbar_expect_tx(&bar[g], (unsigned)((k1 - k0) * kSmoothThreads * sizeof(float)));
+      for (int k = k0; k < k1; ++k) tma_row(tile + k * kSmoothThreads, &map, x0, (int)(p0 + (long long)k * (nr + 1)), &bar[g]);
+    }
+  }
+  // groups known complete; a wait that runs out sets the status word, waits
+  // once more (bounded) for the copies still in flight, and ends the thread
+  int ready = 0;
+  auto need = [&](int row) -> bool {
+    const int g = row / kTmaRows;
+    while (ready <= g) {
+      long spins = 0;
+      while (!mbar_done(&bar[ready], 0))
+        if (++spins > kTmaSpinLimit) return false;
+      ++ready;
+    }
+    return true;
+  };
+  auto give_up = [&]() {
+    if (P.status) atomicExch(P.status, 1);
+    for (int g = ready; g < ng; ++g) {
+      long spins = 0;
+      while (!mbar_done(&bar[g], 0) && ++spins <= kTmaSpinLimit) {
+      }
+    }
+  };
+  const long long x = x0 + (long long)threadIdx.x;
+  if (x >= J) {
+    // a column past the plane's end (zero-filled by the copy): no output, but
+    // the CTA's copies complete before any of its threads may end the CTA
+    if (!need(L - 1)) give_up();
+    return;
+  }
+  const long long bin0 = p0 * J + x;                   // bin of k = 0
+  const long long bin_step = (long long)(nr + 1) * J;  // next plane of the segment
+  const long long lors = (long long)P.V * P.R;
+  const long long lor0 = p0 * lors + fdiv((unsigned)x, P.magic_T);  // x T < 2^32 (host check)
+  const long long lor_step = (long long)(nr + 1) * lors;
+#if PSC_DEBUG
+  if (dbg_idx(P.dbg, kSiteFinColumn, bin0 + (L - 1) * bin_step, P.n_bins) != bin0 + (L - 1) * bin_step ||
+      dbg_idx(P.dbg, kSiteFinLor, lor0 + (L - 1) * lor_step, P.n_bins / P.T) != lor0 + (L - 1) * lor_step) {
+    if (!need(L - 1)) give_up();
+    return;
+  }
+#endif
+  const float* col = tile + threadIdx.x;  // row k at col[k * kSmoothThreads]
+  const Weights& g = P.g[2];
+  float w[2 * KT + NB];
+  if (L >= KT) {
+    if (KT > 0 && !need(KT - 1)) return give_up();
+#pragma unroll
+    for (int r = 0; r < KT; ++r) {  // row r, and row -1 - r reflected onto it
+      const float v = col[r * kSmoothThreads];
+      w[KT + r] = v;
+      w[KT - 1 - r] = v;
+    }
+  } else {
+    if (!need(L - 1)) return give_up();
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) w[j] = col[reflect(j - KT, L) * kSmoothThreads];
+  }
+  const bool use_sens = !P.sens_first && P.sens;
+  const float cf = (float)P.c;
+  const long long step2 = NB * bin_step;
+  double* dst = P.out + bin0;
+  const long long* ap = P.acc + bin0;
+  const long long rs = P.norm_per_lor ? lor_step : bin_step, ss = P.sens_per_lor ? lor_step : bin_step;
+  const double* rp = kNorm ? P.rnorm + (P.norm_per_lor ? lor0 : bin0) : nullptr;
+  const double* sp = use_sens ? P.sens + (P.sens_per_lor ? lor0 : bin0) : nullptr;
+  for (int o0 = 0; o0 < L; o0 += NB) {
+    if (!need(min(o0 + KT + 1, L - 1))) return give_up();
+    const int ra = o0 + KT < L ? o0 + KT : reflect(o0 + KT, L);
+    const int rb = o0 + KT + 1 < L ? o0 + KT + 1 : reflect(o0 + KT + 1, L);
+    w[2 * KT] = col[ra * kSmoothThreads];
+    w[2 * KT + 1] = col[rb * kSmoothThreads];
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j <= 2 * KT; ++j) {
+      s0 = fmaf(g[j], w[j], s0);
+      s1 = fmaf(g[j], w[j + 1], s1);
+    }
+    const bool two = o0 + 1 < L;
+    long long qa0 = 0, qa1 = 0;
+    double fr0 = 1.0, fr1 = 1.0, fs0 = 1.0, fs1 = 1.0;
+    if (kDivide) {
+      qa0 = __ldg(ap);
+      if (two) qa1 = __ldg(ap + bin_step);
+      ap += step2;
+    } else {
+      if (kNorm) {
+        fr0 = __ldg(rp);
+        if (two) fr1 = __ldg(rp + rs);
+        rp += NB * rs;
+      }
+      if (use_sens) {
+        fs0 = __ldg(sp);
+        if (two) fs1 = __ldg(sp + ss);
+        sp += NB * ss;
+      }
+    }
+    dst[0] = axial_epilogue<kDivide, kNorm>(s0, qa0, fr0, fs0, use_sens, cf);
+    if (two) dst[bin_step] = axial_epilogue_fp64<kDivide, kNorm>(s1, qa1, fr1, fs1, use_sens, cf);
+    dst += step2;
+#pragma unroll
+    for (int j = 0; j < 2 * KT; ++j) w[j] = w[NB + j];
+  }
+}
+
+
 template <int KT, bool kDivide, bool kNorm>
 __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>)) smooth_axial_kernel(const __grid_constant__ FinParams P) {
   const int I = P.R * P.T;
@@ -722,10 +908,97 @@ cudaError_t launch_smooth_front(const FinParams& p, cudaStream_t s) {
   return dispatch_kt<ViewL>(p.KT[1], p, dim3(smooth_blocks(I), planes), s);
 }
 
+// the driver's tensor-map encoder, looked up once (no link against libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// The TMA-staged axial pass applies when the FP32 working sinogram can be
+// described as a 2D tensor of n^2 planes of J bins (16-byte aligned base,
+// plane pitch J * 4 a multiple of 16 bytes), segments fit the shared-memory
+// tile (n_rings <= kTmaMaxRings), the window radius is instantiated, x T <
+// 2^32 for every bin x of a plane (exact LOR by multiply-high), and the
+// environment does not switch it off (PSC_AXIAL_TMA=0).  The map describes
+// 256-bin by 1-plane boxes.
+static bool axial_tma_map(const FinParams& p, CUtensorMap* map) {
+  const char* env = std::getenv("PSC_AXIAL_TMA");
+  if (env && env[0] == '0') return false;
+  const long long J = (long long)p.V * p.R * p.T;
+  if (p.KT[2] < 0 || p.n_rings > kTmaMaxRings || J % 4 != 0 || J * p.T >= (1LL << 32) ||
+      ((uintptr_t)p.scratch & 15) != 0)
+    return false;
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)J, (cuuint64_t)p.n_rings * (cuuint64_t)p.n_rings};
+  const cuuint64_t strides[1] = {(cuuint64_t)J * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kSmoothThreads, 1};
+  const cuuint32_t elem[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.scratch, dims, strides, box, elem,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KT, bool kDivide, bool kNorm>
+static cudaError_t run_axial_tma(const FinParams& p, const CUtensorMap& map, dim3 grid, int rows, cudaStream_t s) {
+  const size_t smem = (size_t)rows * kSmoothThreads * sizeof(float);
+  auto k = smooth_axial_tma_kernel<KT, kDivide, kNorm>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kSmoothThreads, smem, s>>>(p, map);
+  return cudaGetLastError();
+}
+
+template <int I = 0, class F>
+static cudaError_t for_window_radius(int kt, F&& f) {
+  constexpr int n = (int)(sizeof(kWindowRadii) / sizeof(kWindowRadii[0]));
+  if constexpr (I == n) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (kt == kWindowRadii[I]) return f(std::integral_constant<int, kWindowRadii[I]>{});
+    return for_window_radius<I + 1>(kt, f);
+  }
+}
+
 cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t s) {
   if (hi <= lo) return cudaSuccess;
   FinParams q = p;
   q.seg0 = lo;
+  CUtensorMap map;
+  if (axial_tma_map(p, &map)) {
+    // segments of at most kTmaShortRows planes in launches of their own,
+    // whose smaller tiles let 6 CTAs share an SM's shared memory (the long
+    // middle segments run 4 per SM)
+    const int n = p.n_rings, S = std::min(kTmaShortRows, n);
+    const int c1 = std::max(lo, std::min(hi, S)), c2 = std::max(c1, std::min(hi, 2 * n - 1 - S));
+    const int cuts[4] = {lo, c1, c2, hi};
+    const long long J = (long long)p.V * p.R * p.T;
+    for (int r = 0; r < 3; ++r) {
+      const int a = cuts[r], b = cuts[r + 1];
+      if (b <= a) continue;
+      int rows = 0;  // the longest segment of [a, b)
+      for (int sg = a; sg < b; ++sg) rows = std::max(rows, n - std::abs(sg - (n - 1)));
+      q.seg0 = a;
+      const dim3 grid(smooth_blocks(J), (unsigned)(b - a));
+      const cudaError_t e = for_window_radius(p.KT[2], [&](auto kt) -> cudaError_t {
+        constexpr int KT = decltype(kt)::value;
+        if (p.divide_acc) return run_axial_tma<KT, true, false>(q, map, grid, rows, s);
+        if (p.rnorm) return run_axial_tma<KT, false, true>(q, map, grid, rows, s);
+        return run_axial_tma<KT, false, false>(q, map, grid, rows, s);
+      });
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   return dispatch_kt<AxialL>(p.KT[2], q, dim3(smooth_blocks((long long)p.R * p.T), (unsigned)((hi - lo) * p.V)), s);
 }
 

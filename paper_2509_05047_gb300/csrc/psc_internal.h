@@ -36,6 +36,7 @@ struct FinParams {
   DebugRecord* dbg;            // bounds-check record of the debug build (nullptr: none)
   int divide_acc;              // output smoothed / (acc * c), 0 where acc == 0 (normalisation sinogram)
   unsigned magic_T;            // ceil(2^32 / T) for exact i / T, 0 when T == 1
+  int* status;                 // set nonzero when a tile wait of the axial pass timed out (or nullptr)
   int K[3];                    // truncation radius per axis (radial, view, axial)
   int KT[3];                   // instantiated window radius >= K, or -1: per-tap loop
   float g[3][2 * kMaxSmoothRadius + 1];  // weights centred on KT (on K when KT = -1), zero-padded

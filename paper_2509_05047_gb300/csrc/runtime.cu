@@ -181,6 +181,10 @@ struct psc_ctx {
   // each zeroed on the launch's stream before use
   DevBuf counters;
   DevBuf dbg;                     // bounds-check record (DebugRecord) of the debug build
+  // host-mapped word the axial pass sets when a bounded wait for its tile
+  // copies ran out (reported by the next finalize call), or nullptr
+  int* status_host = nullptr;
+  int* status_dev = nullptr;
   unsigned long long counter_next = 0;
   // slot fields the transport kernel keeps in global memory, grown on
   // demand; launches on different streams are ordered through cold_done
@@ -453,6 +457,16 @@ int psc_create(psc_ctx** out, int32_t device, uint64_t mem_budget_bytes) {
     delete ctx;
     return cuda_fail(e, "cudaEventCreate");
   }
+  if (cudaHostAlloc((void**)&ctx->status_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+    *ctx->status_host = 0;
+    if (cudaHostGetDevicePointer((void**)&ctx->status_dev, ctx->status_host, 0) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->status_dev = nullptr;
+    }
+  } else {
+    cudaGetLastError();
+    ctx->status_host = nullptr;
+  }
   *out = ctx;
   return PSC_OK;
 }
@@ -464,6 +478,7 @@ void psc_destroy(psc_ctx* ctx) {
   if (ctx->scratch_done) cudaEventDestroy(ctx->scratch_done);
   if (ctx->cold_done) cudaEventDestroy(ctx->cold_done);
   if (ctx->upload) cudaStreamDestroy(ctx->upload);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
   delete ctx;
 }
 
@@ -1319,6 +1334,9 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
     if (norm->scanner != acc->scanner) return fail(PSC_EINVAL, "normalisation sinogram belongs to another scanner");
   }
   if (!std::isfinite(a->scale)) return fail(PSC_EINVAL, "scale must be finite");
+  if (ctx->status_host && __atomic_exchange_n(ctx->status_host, 0, __ATOMIC_ACQ_REL))
+    return fail(PSC_EDEVICE, "an earlier smoothing call on this context stopped: its shared-memory tile copies did "
+                             "not complete within the bounded wait, so that estimate is incomplete");
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const bool cap = capturing(s);
@@ -1340,6 +1358,7 @@ static int finalize_launches(psc_ctx* ctx, const psc_finalize_args* a, double* o
   p.sens_first = a->sens_first ? 1 : 0;
   p.divide_acc = divide;
   p.dbg = (DebugRecord*)ctx->dbg.p;
+  p.status = ctx->status_dev;
   if (a->seg_lo != a->seg_hi) {
     if (a->seg_lo < 0 || a->seg_hi > 2 * d.n_rings - 1 || a->seg_lo > a->seg_hi)
       return fail(PSC_EINVAL, "segment range [%d, %d) outside [0, %d)", (int)a->seg_lo, (int)a->seg_hi,

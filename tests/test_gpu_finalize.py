@@ -322,3 +322,63 @@ def test_smoothed_epilogue_rounds_ties_like_ieee(small):
     out = small.run(sens=s_id, sigma=(0.0, 0.0, 0.0), scale=2.0**32).cpu().numpy()
     np.testing.assert_array_equal(out, acc.astype(np.float64) * sens[..., None])
     small.write_acc(small.acc)
+
+
+@pytest.mark.parametrize("sigma", [(2.0, 2.0, 2.0), (1.0, 0.7, 2.9), (0.6, 1.1, 0.4), (1.5, 1.0, 0.0)])
+@pytest.mark.parametrize("norm_kind", [None, "lor", "bin"])
+@pytest.mark.parametrize("sens_kind", ["lor", "bin"])
+def test_tma_staged_axial_pass_equals_direct_pass(sigma, norm_kind, sens_kind, monkeypatch):
+    """Planes whose bin count is a multiple of 4 (here 20 views x 33 radial x
+    5 TOF = 3300, so the last 256-bin tile of a plane is partial) take the
+    axial pass with TMA-staged shared-memory tiles; PSC_AXIAL_TMA=0 selects
+    the pass that loads its rows directly.  Both must give the same bits (the
+    same arithmetic per bin), for axial radii 8, 12, 2 and 0, with and without
+    a normalisation, per-LOR and per-bin factors, for a segment-restricted
+    call, and for the normalisation sinogram (smooth(acc) / acc); the estimate
+    matches the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_small(n_crystals=40, n_rings=9, n_tof=5, n_rad=33)
+    assert (sc.n_crystals // 2 * sc.n_rad * sc.n_tof) % 4 == 0
+    f = Fin(sc)
+    try:
+        rng = np.random.default_rng(31)
+        acc = rng.integers(0, 1 << 40, size=sc.shape, dtype=np.int64)
+        acc[rng.uniform(size=sc.shape) < 0.3] = 0
+        f.write_acc(acc)
+        shp = {"lor": sc.lor_shape, "bin": sc.shape}
+        sens = rng.uniform(0.5, 1.5, size=shp[sens_kind])
+        norm = rng.uniform(0.2, 2.0, size=shp[norm_kind]) if norm_kind else None
+        if norm is not None:
+            norm.reshape(-1)[:5] = 0.0
+        kw = dict(sens=f.sino(sens, sens_kind == "lor"), sigma=sigma, scale=0.37)
+        if norm is not None:
+            kw["norm"] = f.sino(norm, norm_kind == "lor")
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def both(run):
+            res = []
+            for tma in ("1", "0"):
+                monkeypatch.setenv("PSC_AXIAL_TMA", tma)
+                out = torch.full(sc.shape, np.nan, dtype=torch.float64, device="cuda")
+                run(out)
+                torch.cuda.synchronize()
+                res.append(out.cpu().numpy())
+            np.testing.assert_array_equal(res[0], res[1])
+            return res[0]
+
+        est = both(lambda out: psc.psc_finalize(f.ctx, psc.finalize_args(f.a_id, **kw), out, stream))
+        ref = oracle.finalize(acc, sc.n_rings, sens=sens, norm=norm, sigma=sigma, scale=0.37)
+        np.testing.assert_allclose(est, ref, rtol=SMOOTH_RTOL, atol=1e-300)
+        # segments 3 .. 11 of 17 only: their planes equal the full estimate's
+        part = both(lambda out: psc.psc_finalize(f.ctx, psc.finalize_args(f.a_id, segments=(3, 12), **kw), out,
+                                                 stream))
+        planes = [ra * (sc.n_rings + 1) + (s - sc.n_rings + 1) + k * (sc.n_rings + 1)
+                  for s in range(3, 12) for ra in [max(0, sc.n_rings - 1 - s)]
+                  for k in range(sc.n_rings - abs(s - sc.n_rings + 1))]
+        np.testing.assert_array_equal(part[planes], est[planes])
+        if norm_kind is None and sens_kind == "lor":
+            both(lambda out: psc.psc_norm_sinogram(f.ctx, f.a_id, sigma, out, stream))
+    finally:
+        f.close()
