@@ -210,7 +210,8 @@ def host_memory_state():
     except OSError:
         pass
     keys = ("compact_stall", "compact_fail", "thp_fault_alloc", "thp_fault_fallback", "thp_collapse_alloc",
-            "thp_split_page", "thp_split_pmd", "thp_migration_split", "thp_migration_fail", "pgmigrate_success",
+            "thp_split_page", "thp_split_pmd", "thp_underused_split_page", "thp_deferred_split_page",
+            "thp_migration_split", "thp_migration_fail", "pgmigrate_success",
             "pgmigrate_fail", "pgscan_direct", "pgsteal_direct", "pgmajfault")
     try:
         for line in open("/proc/meminfo"):

@@ -465,7 +465,9 @@ uint64_t psc_resident_bytes(const psc_ctx* ctx);
  * anonymous memory aligned to and advised for transparent huge pages, faulted in, and
  * registered with CUDA for every device (cudaHostRegister, portable).  Huge pages keep
  * the device's translations of the buffer few, so device-to-host copies into it run at
- * the host link's rate even while kernels run.  Independent of any context.
+ * the host link's rate even while kernels run.  Its initial contents are unspecified
+ * (faulted in with a nonzero byte per base page, so that the kernel does not take its
+ * huge pages for unused zero pages and split them).  Independent of any context.
  *   bytes: size (> 0; rounded up to whole huge pages).  *ptr: the buffer, owned by the
  *   caller until psc_host_free.  Errors: PSC_EINVAL (NULL ptr, 0 bytes), PSC_ENOMEM
  *   (mapping failed), PSC_EDEVICE (registration failed; nothing is left allocated). */

@@ -530,7 +530,10 @@ int psc_host_alloc(uint64_t bytes, void** ptr) {
   madvise(p, len, MADV_HUGEPAGE);  // advice only: without it the buffer still works, on base pages
   const long pg = sysconf(_SC_PAGESIZE);
   const size_t step = pg > 0 ? (size_t)pg : 4096;
-  for (size_t i = 0; i < len; i += step) p[i] = 0;  // fault in now, as huge pages where possible
+  // fault in now, as huge pages where possible, with one nonzero byte per
+  // base page: the kernel may split huge pages whose base pages are all
+  // zero (its underused-huge-page shrinker); the contents are unspecified
+  for (size_t i = 0; i < len; i += step) p[i] = 1;
   // where a fault found no free huge page (fragmented memory), collapse each
   // huge-page block now (Linux 6.1+): a block that fails is released and
   // faulted in again, then collapsed once more.  A registered buffer with
@@ -547,7 +550,7 @@ int psc_host_alloc(uint64_t bytes, void** ptr) {
       }
       if (attempt == 1) {     // give the block's memory back and fault it in again
         madvise(b, hp, MADV_DONTNEED);
-        for (size_t i = 0; i < hp; i += step) b[i] = 0;
+        for (size_t i = 0; i < hp; i += step) b[i] = 1;
       }
     }
   }
