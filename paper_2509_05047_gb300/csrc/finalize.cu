@@ -564,7 +564,8 @@ constexpr int kAxialMinCtas = KT >= 0 && KT <= 8 ? (kNorm ? 4 : 6) : 1;
 constexpr int kTmaRows = 8;           // rows per mbarrier group
 constexpr int kTmaMaxRings = 96;      // tiles of at most 96 rows (96 KB of shared memory)
 constexpr int kTmaShortRows = 36;     // segments up to 36 planes: 6 CTAs of 36 KB tiles per SM
-constexpr long kTmaSpinLimit = 1L << 24;  // bounded wait: then the status word is set and the CTA stops
+constexpr long kTmaSpinLimit = 1L << 24;  // a tile wait's bound, in polls: then the status word is set
+constexpr long kTmaFaultSpins = 1L << 12;  // the injected wait's bound (tests)
 
 __device__ __forceinline__ unsigned smem_u32(const void* q) { return (unsigned)__cvta_generic_to_shared(q); }
 
@@ -600,7 +601,10 @@ __device__ __forceinline__ void tma_row(float* dst, const CUtensorMap* map, int 
       : "memory");
 }
 
-template <int KT, bool kDivide, bool kNorm>
+// kFault (an instantiation for tests of the timeout path only): no copies are
+// issued for a tile's first row group, whose wait runs out after
+// kTmaFaultSpins polls; the other groups' copies run and are waited for
+template <int KT, bool kDivide, bool kNorm, bool kFault = false>
 __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
     smooth_axial_tma_kernel(const __grid_constant__ FinParams P, const __grid_constant__ CUtensorMap map) {
   extern __shared__ __align__(128) float tile[];  // [L][kSmoothThreads]
@@ -623,6 +627,7 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
     for (int g = 0; g < ng; ++g) {
       const int k0 = g * kTmaRows, k1 = min(L, k0 + kTmaRows);
       mbar_expect_tx(&bar[g], (unsigned)((k1 - k0) * kSmoothThreads * sizeof(float)));
+      if (kFault && g == 0) continue;  // group 0 expects bytes no copy delivers
       for (int k = k0; k < k1; ++k) tma_row(tile + k * kSmoothThreads, &map, x0, (int)(p0 + (long long)k * (nr + 1)), &bar[g]);
     }
   }
@@ -634,7 +639,7 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
     while (ready <= g) {
       long spins = 0;
       while (!mbar_done(&bar[ready], 0))
-        if (++spins > kTmaSpinLimit) return false;
+        if (++spins > (kFault ? kTmaFaultSpins : kTmaSpinLimit)) return false;
       ++ready;
     }
     return true;
@@ -642,6 +647,7 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
   auto give_up = [&]() {
     if (P.status) atomicExch(P.status, 1);
     for (int g = ready; g < ng; ++g) {
+      if (kFault && g == 0) continue;  // nothing in flight there
       long spins = 0;
       while (!mbar_done(&bar[g], 0) && ++spins <= kTmaSpinLimit) {
       }
@@ -948,10 +954,10 @@ static bool axial_tma_map(const FinParams& p, CUtensorMap* map) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KT, bool kDivide, bool kNorm>
+template <int KT, bool kDivide, bool kNorm, bool kFault = false>
 static cudaError_t run_axial_tma(const FinParams& p, const CUtensorMap& map, dim3 grid, int rows, cudaStream_t s) {
   const size_t smem = (size_t)rows * kSmoothThreads * sizeof(float);
-  auto k = smooth_axial_tma_kernel<KT, kDivide, kNorm>;
+  auto k = smooth_axial_tma_kernel<KT, kDivide, kNorm, kFault>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kSmoothThreads, smem, s>>>(p, map);
@@ -975,6 +981,11 @@ cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t
   q.seg0 = lo;
   CUtensorMap map;
   if (axial_tma_map(p, &map)) {
+    // every tile wait is bounded; PSC_FAULT_TMA_WAIT=1 (tests of the timeout
+    // path) runs the kFault instantiation where there is one (window radius
+    // 8, no normalisation, not the normalisation sinogram)
+    const char* inj = std::getenv("PSC_FAULT_TMA_WAIT");
+    const bool fault = inj && inj[0] == '1' && p.KT[2] == 8 && !p.divide_acc && !p.rnorm;
     // segments of at most kTmaShortRows planes in launches of their own,
     // whose smaller tiles let 6 CTAs share an SM's shared memory (the long
     // middle segments run 4 per SM)
@@ -991,6 +1002,8 @@ cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t
       const dim3 grid(smooth_blocks(J), (unsigned)(b - a));
       const cudaError_t e = for_window_radius(p.KT[2], [&](auto kt) -> cudaError_t {
         constexpr int KT = decltype(kt)::value;
+        if constexpr (KT == 8)
+          if (fault) return run_axial_tma<KT, false, false, true>(q, map, grid, rows, s);
         if (p.divide_acc) return run_axial_tma<KT, true, false>(q, map, grid, rows, s);
         if (p.rnorm) return run_axial_tma<KT, false, true>(q, map, grid, rows, s);
         return run_axial_tma<KT, false, false>(q, map, grid, rows, s);

@@ -382,3 +382,32 @@ def test_tma_staged_axial_pass_equals_direct_pass(sigma, norm_kind, sens_kind, m
             both(lambda out: psc.psc_norm_sinogram(f.ctx, f.a_id, sigma, out, stream))
     finally:
         f.close()
+
+
+def test_tma_tile_wait_timeout_is_reported_and_context_stays_usable(monkeypatch):
+    """The TMA-staged axial pass bounds every wait for its tile copies.  With
+    PSC_FAULT_TMA_WAIT=1 each CTA first waits on an extra barrier that no copy
+    completes (its real copies complete normally): the wait runs out after
+    2^12 polls, the pass stops and sets the context's status word, and the
+    next finalize call reports PSC_EDEVICE.  The one after it runs normally and
+    gives the estimate bit for bit, so the context stays usable."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_small(n_crystals=40, n_rings=9, n_tof=5, n_rad=33)
+    f = Fin(sc)
+    try:
+        rng = np.random.default_rng(7)
+        acc = rng.integers(0, 1 << 40, size=sc.shape, dtype=np.int64)
+        f.write_acc(acc)
+        kw = dict(sens=f.sino(rng.uniform(0.5, 1.5, size=sc.lor_shape), True), sigma=(2.0, 2.0, 2.0), scale=0.37)
+        ref = f.run(**kw).cpu().numpy()
+        monkeypatch.setenv("PSC_FAULT_TMA_WAIT", "1")
+        f.run(**kw)                          # enqueued normally; its waits run out on the device
+        monkeypatch.delenv("PSC_FAULT_TMA_WAIT")
+        with pytest.raises(psc.PscError) as e:
+            f.run(**kw)
+        assert e.value.code == psc.PSC_EDEVICE and "did not complete" in str(e.value)
+        np.testing.assert_array_equal(f.run(**kw).cpu().numpy(), ref)
+    finally:
+        f.close()
