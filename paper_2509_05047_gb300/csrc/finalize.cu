@@ -603,11 +603,12 @@ __device__ __forceinline__ void tma_row(float* dst, const CUtensorMap* map, int 
 
 // kFault (an instantiation for tests of the timeout path only): no copies are
 // issued for a tile's first row group, whose wait runs out after
-// kTmaFaultSpins polls; the other groups' copies run and are waited for
-template <int KT, bool kDivide, bool kNorm, bool kFault = false>
-__global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
+// kTmaFaultSpins polls; the other groups' copies run and are waited for.
+// TW: the tile's width in bins, which is also the CTA's thread count.
+template <int KT, bool kDivide, bool kNorm, bool kFault = false, int TW = kSmoothThreads>
+__global__ void __launch_bounds__(TW, (kAxialMinCtas<KT, kNorm> * kSmoothThreads / TW))
     smooth_axial_tma_kernel(const __grid_constant__ FinParams P, const __grid_constant__ CUtensorMap map) {
-  extern __shared__ __align__(128) float tile[];  // [L][kSmoothThreads]
+  extern __shared__ __align__(128) float tile[];  // [L][TW]
   __shared__ __align__(8) unsigned long long bar[kTmaMaxRings / kTmaRows];
   constexpr int NB = 2;
   const int nr = P.n_rings;
@@ -616,7 +617,7 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
   const int L = nr - abs(d);
   const long long p0 = (long long)max(0, -d) * (nr + 1) + d;
   const long long J = (long long)P.V * P.R * P.T;
-  const int x0 = (int)blockIdx.x * kSmoothThreads;  // the chunk's first bin in a plane
+  const int x0 = (int)blockIdx.x * TW;  // the chunk's first bin in a plane
   const int ng = (L + kTmaRows - 1) / kTmaRows;
   if (threadIdx.x == 0) {
     for (int g = 0; g < ng; ++g) mbar_init(&bar[g], 1);
@@ -626,9 +627,9 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
   if (threadIdx.x == 0) {
     for (int g = 0; g < ng; ++g) {
       const int k0 = g * kTmaRows, k1 = min(L, k0 + kTmaRows);
-      mbar_expect_tx(&bar[g], (unsigned)((k1 - k0) * kSmoothThreads * sizeof(float)));
+      mbar_expect_tx(&bar[g], (unsigned)((k1 - k0) * TW * sizeof(float)));
       if (kFault && g == 0) continue;  // group 0 expects bytes no copy delivers
-      for (int k = k0; k < k1; ++k) tma_row(tile + k * kSmoothThreads, &map, x0, (int)(p0 + (long long)k * (nr + 1)), &bar[g]);
+      for (int k = k0; k < k1; ++k) tma_row(tile + k * TW, &map, x0, (int)(p0 + (long long)k * (nr + 1)), &bar[g]);
     }
   }
   // groups known complete; a wait that runs out sets the status word, waits
@@ -672,21 +673,21 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
     return;
   }
 #endif
-  const float* col = tile + threadIdx.x;  // row k at col[k * kSmoothThreads]
+  const float* col = tile + threadIdx.x;  // row k at col[k * TW]
   const Weights& g = P.g[2];
   float w[2 * KT + NB];
   if (L >= KT) {
     if (KT > 0 && !need(KT - 1)) return give_up();
 #pragma unroll
     for (int r = 0; r < KT; ++r) {  // row r, and row -1 - r reflected onto it
-      const float v = col[r * kSmoothThreads];
+      const float v = col[r * TW];
       w[KT + r] = v;
       w[KT - 1 - r] = v;
     }
   } else {
     if (!need(L - 1)) return give_up();
 #pragma unroll
-    for (int j = 0; j < 2 * KT; ++j) w[j] = col[reflect(j - KT, L) * kSmoothThreads];
+    for (int j = 0; j < 2 * KT; ++j) w[j] = col[reflect(j - KT, L) * TW];
   }
   const bool use_sens = !P.sens_first && P.sens;
   const float cf = (float)P.c;
@@ -700,8 +701,8 @@ __global__ void __launch_bounds__(kSmoothThreads, (kAxialMinCtas<KT, kNorm>))
     if (!need(min(o0 + KT + 1, L - 1))) return give_up();
     const int ra = o0 + KT < L ? o0 + KT : reflect(o0 + KT, L);
     const int rb = o0 + KT + 1 < L ? o0 + KT + 1 : reflect(o0 + KT + 1, L);
-    w[2 * KT] = col[ra * kSmoothThreads];
-    w[2 * KT + 1] = col[rb * kSmoothThreads];
+    w[2 * KT] = col[ra * TW];
+    w[2 * KT + 1] = col[rb * TW];
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
     for (int j = 0; j <= 2 * KT; ++j) {
@@ -936,7 +937,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 2^32 for every bin x of a plane (exact LOR by multiply-high), and the
 // environment does not switch it off (PSC_AXIAL_TMA=0).  The map describes
 // 256-bin by 1-plane boxes.
-static bool axial_tma_map(const FinParams& p, CUtensorMap* map) {
+static bool axial_tma_map(const FinParams& p, CUtensorMap* map, int tw) {
   const char* env = std::getenv("PSC_AXIAL_TMA");
   if (env && env[0] == '0') return false;
   const long long J = (long long)p.V * p.R * p.T;
@@ -947,20 +948,20 @@ static bool axial_tma_map(const FinParams& p, CUtensorMap* map) {
   if (!encode) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)J, (cuuint64_t)p.n_rings * (cuuint64_t)p.n_rings};
   const cuuint64_t strides[1] = {(cuuint64_t)J * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kSmoothThreads, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)tw, 1};
   const cuuint32_t elem[2] = {1, 1};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.scratch, dims, strides, box, elem,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KT, bool kDivide, bool kNorm, bool kFault = false>
+template <int KT, bool kDivide, bool kNorm, bool kFault = false, int TW = kSmoothThreads>
 static cudaError_t run_axial_tma(const FinParams& p, const CUtensorMap& map, dim3 grid, int rows, cudaStream_t s) {
-  const size_t smem = (size_t)rows * kSmoothThreads * sizeof(float);
-  auto k = smooth_axial_tma_kernel<KT, kDivide, kNorm, kFault>;
+  const size_t smem = (size_t)rows * TW * sizeof(float);
+  auto k = smooth_axial_tma_kernel<KT, kDivide, kNorm, kFault, TW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, kSmoothThreads, smem, s>>>(p, map);
+  k<<<grid, TW, smem, s>>>(p, map);
   return cudaGetLastError();
 }
 
@@ -979,16 +980,17 @@ cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t
   if (hi <= lo) return cudaSuccess;
   FinParams q = p;
   q.seg0 = lo;
-  CUtensorMap map;
-  if (axial_tma_map(p, &map)) {
+  CUtensorMap map, map_narrow;
+  if (axial_tma_map(p, &map, kSmoothThreads) && axial_tma_map(p, &map_narrow, kSmoothThreads / 2)) {
     // every tile wait is bounded; PSC_FAULT_TMA_WAIT=1 (tests of the timeout
     // path) runs the kFault instantiation where there is one (window radius
     // 8, no normalisation, not the normalisation sinogram)
     const char* inj = std::getenv("PSC_FAULT_TMA_WAIT");
     const bool fault = inj && inj[0] == '1' && p.KT[2] == 8 && !p.divide_acc && !p.rnorm;
     // segments of at most kTmaShortRows planes in launches of their own,
-    // whose smaller tiles let 6 CTAs share an SM's shared memory (the long
-    // middle segments run 4 per SM)
+    // whose smaller tiles let 6 CTAs share an SM's shared memory; the long
+    // middle segments run tiles half as wide (128 bins, half the shared
+    // memory per CTA) in CTAs of 128 threads
     const int n = p.n_rings, S = std::min(kTmaShortRows, n);
     const int c1 = std::max(lo, std::min(hi, S)), c2 = std::max(c1, std::min(hi, 2 * n - 1 - S));
     const int cuts[4] = {lo, c1, c2, hi};
@@ -999,11 +1001,21 @@ cudaError_t launch_smooth_axial(const FinParams& p, int lo, int hi, cudaStream_t
       int rows = 0;  // the longest segment of [a, b)
       for (int sg = a; sg < b; ++sg) rows = std::max(rows, n - std::abs(sg - (n - 1)));
       q.seg0 = a;
-      const dim3 grid(smooth_blocks(J), (unsigned)(b - a));
+      const bool narrow = rows > kTmaShortRows;
+      constexpr int kNarrow = kSmoothThreads / 2;
+      const dim3 grid((unsigned)((J + (narrow ? kNarrow : kSmoothThreads) - 1) / (narrow ? kNarrow : kSmoothThreads)),
+                      (unsigned)(b - a));
       const cudaError_t e = for_window_radius(p.KT[2], [&](auto kt) -> cudaError_t {
         constexpr int KT = decltype(kt)::value;
         if constexpr (KT == 8)
-          if (fault) return run_axial_tma<KT, false, false, true>(q, map, grid, rows, s);
+          if (fault)
+            return narrow ? run_axial_tma<KT, false, false, true, kNarrow>(q, map_narrow, grid, rows, s)
+                          : run_axial_tma<KT, false, false, true>(q, map, grid, rows, s);
+        if (narrow) {
+          if (p.divide_acc) return run_axial_tma<KT, true, false, false, kNarrow>(q, map_narrow, grid, rows, s);
+          if (p.rnorm) return run_axial_tma<KT, false, true, false, kNarrow>(q, map_narrow, grid, rows, s);
+          return run_axial_tma<KT, false, false, false, kNarrow>(q, map_narrow, grid, rows, s);
+        }
         if (p.divide_acc) return run_axial_tma<KT, true, false>(q, map, grid, rows, s);
         if (p.rnorm) return run_axial_tma<KT, false, true>(q, map, grid, rows, s);
         return run_axial_tma<KT, false, false>(q, map, grid, rows, s);

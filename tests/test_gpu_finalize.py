@@ -411,3 +411,48 @@ def test_tma_tile_wait_timeout_is_reported_and_context_stays_usable(monkeypatch)
         np.testing.assert_array_equal(f.run(**kw).cpu().numpy(), ref)
     finally:
         f.close()
+
+
+@pytest.mark.parametrize("norm_kind", [None, "lor"])
+def test_tma_axial_pass_on_long_segments_equals_direct_pass(norm_kind, monkeypatch):
+    """With more than 36 rings the longest ring-difference segments (here 37
+    to 40 planes) take the TMA-staged axial pass on 128-bin tiles in CTAs of
+    128 threads, the shorter ones 256-bin tiles.  Both must give the bits of
+    the pass that loads its rows directly (PSC_AXIAL_TMA=0), with and without a
+    normalisation and for the normalisation sinogram; the estimate matches
+    the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc = W.scanner_small(n_crystals=40, n_rings=40, n_tof=5, n_rad=33)
+    f = Fin(sc)
+    try:
+        rng = np.random.default_rng(41)
+        acc = rng.integers(0, 1 << 40, size=sc.shape, dtype=np.int64)
+        acc[rng.uniform(size=sc.shape) < 0.3] = 0
+        f.write_acc(acc)
+        sens = rng.uniform(0.5, 1.5, size=sc.lor_shape)
+        norm = rng.uniform(0.2, 2.0, size=sc.lor_shape) if norm_kind else None
+        kw = dict(sens=f.sino(sens, True), sigma=(1.5, 1.0, 2.0), scale=0.37)
+        if norm is not None:
+            kw["norm"] = f.sino(norm, True)
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def both(run):
+            res = []
+            for tma in ("1", "0"):
+                monkeypatch.setenv("PSC_AXIAL_TMA", tma)
+                out = torch.full(sc.shape, np.nan, dtype=torch.float64, device="cuda")
+                run(out)
+                torch.cuda.synchronize()
+                res.append(out.cpu().numpy())
+            np.testing.assert_array_equal(res[0], res[1])
+            return res[0]
+
+        est = both(lambda out: psc.psc_finalize(f.ctx, psc.finalize_args(f.a_id, **kw), out, stream))
+        ref = oracle.finalize(acc, sc.n_rings, sens=sens, norm=norm, sigma=(1.5, 1.0, 2.0), scale=0.37)
+        np.testing.assert_allclose(est, ref, rtol=SMOOTH_RTOL, atol=1e-300)
+        if norm is None:
+            both(lambda out: psc.psc_norm_sinogram(f.ctx, f.a_id, (1.5, 1.0, 2.0), out, stream))
+    finally:
+        f.close()
