@@ -456,3 +456,45 @@ def test_tma_axial_pass_on_long_segments_equals_direct_pass(norm_kind, monkeypat
             both(lambda out: psc.psc_norm_sinogram(f.ctx, f.a_id, (1.5, 1.0, 2.0), out, stream))
     finally:
         f.close()
+
+
+def _f32_rne(v):
+    """float32 nearest (ties to even) of the non-negative integer v, from its
+    bits: the value the conversion must give."""
+    v = int(v)
+    if v < (1 << 24):
+        return float(v)
+    e = v.bit_length() - 24
+    q, r = divmod(v, 1 << e)
+    half = 1 << (e - 1)
+    if r > half or (r == half and q & 1):
+        q += 1
+    return float(q << e)
+
+
+def test_accumulator_conversion_rounds_like_ieee(small):
+    """The radial pass converts int64 accumulators to FP32 on the integer
+    pipes (leading bit, shift, round half to even on the dropped bits): with
+    zero-width windows and scale 2^32 the estimate is that FP32 value
+    widened, so every bin must equal the round-to-nearest-even FP32 value of
+    its accumulator: values on rounding ties (25 significant bits, last one
+    set) at every shift, ties broken only by a bit far below, values just
+    under powers of two, up to 2^63 - 1, and random magnitudes."""
+    rng = np.random.default_rng(17)
+    shape = small.sc.shape
+    n = int(np.prod(shape))
+    sh = rng.integers(0, 39, size=n)
+    acc = ((rng.integers(1 << 24, 1 << 25, size=n) | 1) << sh)
+    sticky = rng.uniform(size=n) < 0.2
+    acc[sticky] |= 1                                  # a tie broken far below
+    mag = rng.uniform(size=n) < 0.3
+    acc[mag] = rng.integers(0, 1 << 62, size=mag.sum()) >> rng.integers(0, 62, size=mag.sum())
+    acc[:64] = [(1 << k) - 1 for k in range(1, 64)] + [0]
+    acc[64:128] = [(1 << 24) + 1 + (1 << 40) * k for k in range(64)]
+    acc[-1] = (1 << 63) - 1
+    acc = acc.astype(np.int64).reshape(shape)
+    exp = np.array([_f32_rne(v) for v in acc.ravel()]).reshape(shape)
+    np.testing.assert_array_equal(exp, acc.astype(np.float32).astype(np.float64))  # numpy agrees
+    small.write_acc(acc)
+    np.testing.assert_array_equal(small.run(sigma=(0.0, 0.0, 0.0), scale=2.0**32).cpu().numpy(), exp)
+    small.write_acc(small.acc)
