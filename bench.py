@@ -259,6 +259,11 @@ TRANSPORT_DRAM_BYTES_PER_HISTORY = (113.73e6 + 24.62e6) / 2e7  # ncu dram bytes 
 # intermediates on top: radial 8 + 4, view 4 + 4, axial 4 + 8 = 32.
 FINALIZE_METHOD_BYTES_PER_BIN = 16
 FINALIZE_DESIGN_BYTES_PER_BIN = 32
+# DRAM bytes (read + write) per bin of the smoothing launches of one
+# finalize, from an ncu capture of the paper-scale scanner cut to 5 rings (27
+# TOF bins, 67.6 M bins; profiles/finalize_traffic_5_rings_27tof.md): the
+# traffic grows with the bins, so it scales to the full sinogram
+FINALIZE_DRAM_BYTES_PER_BIN = (1109.3e6 + 884.0e6) / 67_586_400
 
 
 def transport_ops(st):
@@ -537,11 +542,13 @@ def run_native(a):
     fin_gbs = method_b * sc.n_bins / (phase[2] / 1e3) / 1e9
     design_gbs = (FINALIZE_DESIGN_BYTES_PER_BIN + 8.0 / sc.n_tof) * sc.n_bins / (phase[2] / 1e3) / 1e9
     finalize_roofline = {"bound": "hbm", "achieved": round(fin_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": round(fin_gbs / peaks["hbm_gbs"], 4), "traffic": None,
+                         "frac": round(fin_gbs / peaks["hbm_gbs"], 4),
+                         "traffic": round(FINALIZE_DRAM_BYTES_PER_BIN * sc.n_bins),
                          "bytes_per_bin": round(method_b, 3),
                          "design_bytes_per_bin": round(FINALIZE_DESIGN_BYTES_PER_BIN + 8.0 / sc.n_tof, 3),
                          "design_frac": round(design_gbs / peaks["hbm_gbs"], 4),
-                         "kernels": "psc::smooth_{radial,view,axial}_kernel", "ms": round(float(phase[2]), 3),
+                         "kernels": "psc::smooth_radial_kernel, psc::smooth_view_kernel, psc::smooth_axial_tma_kernel",
+                         "ms": round(float(phase[2]), 3),
                          "peak_source": f"{src} copy bandwidth"}
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
